@@ -1,0 +1,105 @@
+"""CPU oracle for IWPP morphological reconstruction — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+(and its ``--impl reference`` arm) may import this package. The product library
+(``paper_1605_00930_gb300``) never imports it and shares no code with it.
+
+Contents
+  * ``iwpp_oracle.c`` — Vincent's hybrid reconstruction (Sec. 3.1, Algorithm 7),
+    single-threaded C, built here with gcc into ``liboracle.so``.
+  * ``bruteforce.py`` — Algorithm 1 (Jacobi iteration of Eq. "recon") in numpy.
+  * ``features.py`` / ``mlp.py`` — plain numpy definitions of the per-tile
+    features and of the 16-64-64-2 MLP used by the learned schedule.
+
+Parity status: reconstruction is pinned by brute force, hand-worked cases,
+invariants, duality, threshold decomposition and the binary special case
+(connected components); see tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "iwpp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+DTYPES = {np.dtype(np.uint8): 0, np.dtype(np.uint16): 1}
+OPS = {"dilate": 0, "erode": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (portable C11, no host-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            lib.oracle_reconstruct.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_reconstruct.restype = ctypes.c_int
+            lib.oracle_precondition_ok.argtypes = [ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                                   ctypes.c_int]
+            lib.oracle_precondition_ok.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(marker: np.ndarray, mask: np.ndarray):
+    if marker.shape != mask.shape or marker.ndim != 2:
+        raise ValueError("marker and mask must be equal-shape 2-D arrays")
+    if marker.dtype != mask.dtype or marker.dtype not in DTYPES:
+        raise ValueError("marker and mask must both be uint8 or both uint16")
+
+
+def reconstruct(marker: np.ndarray, mask: np.ndarray, conn: int = 8, op: str = "dilate",
+                return_pops: bool = False):
+    """Vincent's hybrid reconstruction of ``mask`` from ``marker`` (a new array)."""
+    _check(marker, mask)
+    lib = _load()
+    J = np.ascontiguousarray(marker).copy()
+    I = np.ascontiguousarray(mask)
+    pops = ctypes.c_uint64(0)
+    rc = lib.oracle_reconstruct(J.ctypes.data, I.ctypes.data, J.shape[0], J.shape[1], int(conn),
+                                OPS[op], DTYPES[J.dtype], ctypes.byref(pops))
+    if rc != 0:
+        raise ValueError(f"oracle_reconstruct failed with code {rc}")
+    return (J, int(pops.value)) if return_pops else J
+
+
+def precondition_ok(marker: np.ndarray, mask: np.ndarray, op: str = "dilate") -> bool:
+    _check(marker, mask)
+    lib = _load()
+    J = np.ascontiguousarray(marker)
+    I = np.ascontiguousarray(mask)
+    rc = lib.oracle_precondition_ok(J.ctypes.data, I.ctypes.data, J.shape[0], J.shape[1],
+                                    OPS[op], DTYPES[J.dtype])
+    if rc < 0:
+        raise ValueError("bad argument")
+    return rc == 1
+
+
+def reconstruct_many(items, threads: int | None = None):
+    """Reconstruct a list of (marker, mask, conn, op) tuples on ``threads`` host
+    threads, one image per thread at a time (the C call releases the GIL)."""
+    _load()
+    threads = threads or len(os.sched_getaffinity(0))
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(lambda it: reconstruct(*it), items))

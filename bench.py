@@ -1,0 +1,341 @@
+"""Benchmark: Gpixels/s of bit-exact morphological reconstruction on GB300.
+
+Default workload (one step): the 4096 x 4096 u8 tissue-like blob field (2000 blobs,
+h-dome marker h = 30), reconstructed by dilation with 8- and with 4-connectivity
+(2 x 16.8 Mpx per step). Inputs are seeded synthetic data; the working set fits in
+L2, so L2 is flushed (256 MiB write) before every timed step, and the marker is
+restored by a device copy, both outside the timed events.
+
+Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle (Vincent's
+hybrid, single-threaded C) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gpixels/s morph. reconstruction (bit-exact); batched+learned vs plain; %HBM peak"
+UNIT = "Gpixels/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(name: str):
+    from paper_1605_00930_gb300 import synth
+    if name == "tissue4096":
+        c = synth.tissue_case()
+        cases = [(c.marker, c.mask, 8, "dilate"), (c.marker, c.mask, 4, "dilate")]
+        desc = ("tissue 4096x4096 u8: 2000 blobs (r 5-40, peak 80-255) over U{0..30} noise, "
+                "h-dome marker h=30, dilation with conn 8 and conn 4")
+    elif name == "noiseblur512":
+        c = synth.noise_blur_case()
+        cases = [(c.marker, c.mask, 8, "dilate")]
+        desc = "noise-blur 512x512 u8, marker = mask-40, dilation conn 8"
+    elif name == "seeds16384":
+        c = synth.sparse_seed_case()
+        cases = [(c.marker, c.mask, 8, "dilate")]
+        desc = "blob field 16384x16384 u8, 2000 blobs, 1000 seed pixels, dilation conn 8"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return cases, desc
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks / throttle reasons in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows, self.proc, self.gpu = [], None, gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self, t0: float, t1: float):
+        if not self.rows:
+            return None
+        inside = [r for t, r in self.rows if t0 <= t <= t1] or [self.rows[-1][1]]
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in inside:
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+def _traffic_from_profiles(kernel: str):
+    """ncu DRAM bytes per launch recorded under profiles/ for the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1605_00930_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1605_00930_gb300", "csrc", f), "rb").read())
+    digest = h.hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    from paper_1605_00930_gb300 import build as B
+    B.build()
+    from paper_1605_00930_gb300 import iwpp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cases, desc = _workload(args.workload)
+    stream = torch.cuda.current_stream()
+    pix_per_step = sum(c[1].size for c in cases)
+    bytes_per_px = [c[1].dtype.itemsize for c in cases]
+
+    dev_cases = []
+    for marker, mask, conn, op in cases:
+        m0 = torch.from_numpy(marker).to(dev)
+        I = torch.from_numpy(mask).to(dev)
+        m = torch.empty_like(m0)
+        R = iwpp.Reconstructor(mask.shape[0], mask.shape[1], m0.dtype, None, dev)
+        dev_cases.append((m0, I, m, R, conn, op))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(ev=None):
+        for k, (m0, I, m, R, conn, op) in enumerate(dev_cases):
+            if ev is not None:
+                ev[k][0].record(stream)
+            rc = R.phase("scan", m, I, conn, op, stream)
+            if ev is not None:
+                ev[k][1].record(stream)
+            rc |= R.phase("drain", m, I, conn, op, stream)
+            if ev is not None:
+                ev[k][2].record(stream)
+            if rc != 0:
+                raise RuntimeError(iwpp.STATUS.get(rc))
+
+    def prep():
+        for (m0, I, m, R, conn, op) in dev_cases:
+            m.copy_(m0)
+        flush.fill_(1)
+
+    # correctness of the timed configuration (checked once against the oracle on rank 0)
+    prep()
+    step()
+    for (m0, I, m, R, conn, op) in dev_cases:
+        st = R.status(stream)
+        if st != 0:
+            raise RuntimeError(f"device status {iwpp.STATUS.get(st)}")
+    for _ in range(args.warmup):
+        prep()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in dev_cases] for _ in range(args.steps)]
+    gpu_index = dev.index
+    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(gpu_index)).split(",")[0])
+                      if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else gpu_index) as cs:
+        time.sleep(0.25)
+        t0 = time.time()
+        for i in range(args.steps):
+            prep()
+            step(evs[i])
+        torch.cuda.synchronize()
+        t1 = time.time()
+        if t1 - t0 < 0.3:
+            time.sleep(0.3 - (t1 - t0))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    scan_ms = sum(e[k][0].elapsed_time(e[k][1]) for e in evs for k in range(len(dev_cases)))
+    drain_ms = sum(e[k][1].elapsed_time(e[k][2]) for e in evs for k in range(len(dev_cases)))
+    total_ms = scan_ms + drain_ms
+    ms_per_step = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_per_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    value = world * pix_per_step / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the public call with host buffers
+    host_in = [(torch.from_numpy(c[0]).pin_memory(), torch.from_numpy(c[1]).pin_memory()) for c in cases]
+    host_out = [torch.empty_like(h[0]).pin_memory() for h in host_in]
+    h2d = sum(h[0].numel() * h[0].element_size() + h[1].numel() * h[1].element_size() for h in host_in)
+    d2h = sum(h.numel() * h.element_size() for h in host_out)
+
+    def e2e_step():
+        for k, (m0, I, m, R, conn, op) in enumerate(dev_cases):
+            m.copy_(host_in[k][0], non_blocking=True)
+            I.copy_(host_in[k][1], non_blocking=True)
+            rc = R(m, I, conn, op, stream)
+            if rc != 0:
+                raise RuntimeError(iwpp.STATUS.get(rc))
+            host_out[k].copy_(m, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    n_e2e = max(3, min(args.steps, 50))
+    te0 = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te0) / n_e2e
+    for k, (m0, I, m, R, conn, op) in enumerate(dev_cases):
+        if R.status(stream) != 0:
+            raise RuntimeError("device error in e2e run")
+
+    if rank != 0:
+        return None
+    peak, peak_kind = _peaks()
+    s = bytes_per_px[0]
+    nl = len(dev_cases)
+    dominant = "drain_kernel" if drain_ms >= scan_ms else "scan_kernel"
+    dom_ms = (drain_ms if dominant == "drain_kernel" else scan_ms) / (args.steps * nl)
+    alg_bytes = 3 * s * cases[0][1].size   # compulsory bytes of one reconstruction: read J, I, write J
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = _traffic_from_profiles(dominant)
+    cpu = cpu_baseline(cases) if rank == 0 and world == 1 and not args.no_cpu else None
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": desc, "pixels_per_step": pix_per_step, "form": "plain per-image",
+                   "plan": iwpp.iwpp_default_plan().as_dict(),
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "timing": "CUDA events around the scan and drain launches of each step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "phases_ms_per_step": {"scan_kernel": round(scan_ms / args.steps, 4),
+                               "drain_kernel": round(drain_ms / args.steps, 4)},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
+                     "traffic": traffic,
+                     "alg_bytes_per_launch": alg_bytes,
+                     "path_frac": round(3 * s * pix_per_step / (ms_per_step * 1e-3) / 1e9 / peak, 5)},
+        "e2e": {"value": round(world * pix_per_step / e2e_s / 1e9, 3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * nl * args.steps,
+        "clocks": cs.summary(t0, t1),
+        "cpu_baseline": cpu,
+    }
+    return out
+
+
+def cpu_baseline(cases, budget_s: float = 12.0):
+    import oracle
+    oracle.build()
+    done_px, t0 = 0, time.perf_counter()
+    reps = 0
+    while True:
+        for marker, mask, conn, op in cases:
+            oracle.reconstruct(marker, mask, conn, op)
+            done_px += mask.size
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 5:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done_px / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full pass(es) of the workload ({done_px} px), single-threaded C oracle"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    cases, desc = _workload(args.workload)
+    pix = sum(c[1].size for c in cases)
+    for _ in range(args.warmup):
+        for c in cases:
+            oracle.reconstruct(*c)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for c in cases:
+            oracle.reconstruct(*c)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = pix / dt / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": desc, "pixels_per_step": pix},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "every step is the full workload, single-threaded C oracle"},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tissue4096", choices=["tissue4096", "noiseblur512", "seeds16384"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * iwpp.h — C ABI of the GB300 (sm_103a) library for the Irregular Wavefront
+ * Propagation Pattern (IWPP): grayscale morphological reconstruction by
+ * dilation and its dual, reconstruction by erosion (fill-holes).
+ *
+ * What is computed (Sec. 2.1.2, Eq. "recon"; Sec. 3.1, Algorithm 7):
+ *   given a mask image I and a marker image J with J <= I pixelwise, the
+ *   reconstruction R is the stable point of J <- delta_G(J) ^ I, where delta_G
+ *   is the elementary dilation over the 4- or 8-neighbourhood G restricted to
+ *   the image and ^ is the pixelwise minimum. op = IWPP_ERODE computes the dual,
+ *   the stable point of J <- eps_G(J) v I from a marker J >= I; with
+ *   J = I on the image border and the maximum value inside, that is the
+ *   fill-holes operator of Sec. 3.3. The result is unique, so it does not
+ *   depend on the order in which the library propagates values.
+ *
+ * Conventions shared by every call:
+ *   - Images are row-major and contiguous (pitch = W elements), u8 or u16,
+ *     in DEVICE memory, base address 16-byte aligned. The caller owns them.
+ *   - marker_inout holds J on entry and R on exit (the paper's J is both
+ *     input and output). mask is only read.
+ *   - H >= 1, W >= 1, H * W < 2^32 per image; connectivity is 4 or 8 (the
+ *     hexagonal 6-connectivity that Sec. 2.1.2 also names is not supported).
+ *   - The workspace is caller-owned device memory of at least the size the
+ *     matching *_workspace_bytes call returns, 256-byte aligned. The library
+ *     allocates nothing on these paths and keeps no device state between calls.
+ *     Calls on different streams are safe when their workspaces and images
+ *     differ.
+ *   - Host-detectable errors return at once with nothing enqueued. Errors the
+ *     device finds (precondition violation, queue exhaustion, watchdog timeout)
+ *     are written to a status word inside the workspace; read it with
+ *     iwpp_sync_status. When it reports IWPP_ERR_PRECONDITION the output is
+ *     unspecified.
+ *   - All calls are asynchronous on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream) and perform no host synchronisation, except
+ *     iwpp_sync_status and the iwpp_autotune helper.
+ */
+#ifndef IWPP_H
+#define IWPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IWPP_API __attribute__((visibility("default")))
+#else
+#define IWPP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { IWPP_U8 = 0, IWPP_U16 = 1 } iwpp_dtype;
+typedef enum { IWPP_DILATE = 0, IWPP_ERODE = 1 } iwpp_op;
+
+typedef enum {
+    IWPP_OK = 0,
+    IWPP_ERR_ARG = 1,          /* bad argument (null, size, enum, alignment)  */
+    IWPP_ERR_PRECONDITION = 2, /* marker > mask (dilate) / marker < mask (erode) somewhere */
+    IWPP_ERR_WORKSPACE = 3,    /* workspace missing, misaligned or too small   */
+    IWPP_ERR_QUEUE_FULL = 4,   /* a propagation queue ran out of room          */
+    IWPP_ERR_TIMEOUT = 5,      /* the persistent kernel's watchdog expired     */
+    IWPP_ERR_CUDA = 6,         /* a CUDA runtime call failed                   */
+    IWPP_ERR_INTERNAL = 7      /* an internal consistency check failed         */
+} iwpp_status;
+
+/*
+ * Execution plan: the knobs of the propagation engine. None of them can change
+ * the result (the reconstruction is unique); they change only the work done.
+ *   tile_h, tile_w     tile shape; must be one of the compiled shapes
+ *                      (64x64, 32x64, 64x128 — see iwpp_tile_shape_supported)
+ *   sweeps             raster + anti-raster sweep pairs run over every tile
+ *                      before the queue phase (Algorithm 7's scanning phase,
+ *                      tile-local); 0 = queue mode from the start
+ *   revisit_sweeps     sweep pairs run at the start of every first visit of
+ *                      a tile by the persistent kernel (normally 0)
+ *   smem_queue_cap     entries of each of the two shared-memory wave queues
+ *                      of a CTA; waves larger than this spill into the CTA's
+ *                      global overflow queue (16 .. tile_h * tile_w)
+ *   blocks_per_sm      persistent-kernel CTAs per SM (0 = occupancy maximum)
+ *   watchdog_ns        the persistent kernel gives up with IWPP_ERR_TIMEOUT
+ *                      when a wait for work lasts longer than this
+ *                      (0 = default, 10 s)
+ */
+typedef struct {
+    int32_t tile_h, tile_w;
+    int32_t sweeps;
+    int32_t revisit_sweeps;
+    int32_t smem_queue_cap;
+    int32_t blocks_per_sm;
+    int64_t watchdog_ns;
+} iwpp_plan;
+
+/* Fills *plan with the static default schedule. Returns IWPP_OK. */
+IWPP_API int iwpp_default_plan(iwpp_plan *plan);
+
+/* 1 if (tile_h, tile_w) is a compiled tile shape, else 0. */
+IWPP_API int iwpp_tile_shape_supported(int32_t tile_h, int32_t tile_w);
+
+/* Workspace bytes needed by iwpp_reconstruct / iwpp_reconstruct_plan for one
+ * H x W image on the current device under `plan` (NULL = default plan).
+ * Returns 0 for invalid sizes. */
+IWPP_API size_t iwpp_workspace_bytes(int64_t H, int64_t W, int dtype, const iwpp_plan *plan);
+
+/*
+ * Reconstruction of one image (Sec. 3.1, Algorithm 7; Sec. 3.3 for
+ * op = IWPP_ERODE). Enqueues, on `stream`: a workspace reset, one
+ * tile-parallel kernel that checks the precondition, runs the tile-local
+ * raster / anti-raster sweeps and collects the tiles whose pixels can still
+ * propagate (the initial frontier), and one persistent kernel that drains the
+ * frontier with shared-memory wave queues until no tile can change.
+ * Returns IWPP_OK or a host-detected error code; device-side errors go to the
+ * workspace status word (see iwpp_sync_status).
+ */
+IWPP_API int iwpp_reconstruct(void *marker_inout, const void *mask, int64_t H, int64_t W,
+                     int connectivity, int op, int dtype, void *workspace, size_t ws_bytes,
+                     void *stream);
+
+/* As iwpp_reconstruct, under an explicit plan (NULL = default plan). */
+IWPP_API int iwpp_reconstruct_plan(void *marker_inout, const void *mask, int64_t H, int64_t W,
+                          int connectivity, int op, int dtype, const iwpp_plan *plan,
+                          void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * The two steps of iwpp_reconstruct_plan, for callers that time or overlap them:
+ * iwpp_scan resets the workspace and runs the tile-parallel scan kernel
+ * (precondition check, `plan->sweeps` tile-local raster / anti-raster sweep pairs
+ * of Algorithm 7, and frontier initialisation: the tiles whose pixels can still
+ * be raised are queued); iwpp_drain then runs the persistent kernel that drains
+ * the queued tiles (Algorithm 7's irregular propagation phase). Calling
+ * iwpp_scan and then iwpp_drain with identical arguments on one stream is exactly
+ * iwpp_reconstruct_plan. Same arguments, ownership and errors.
+ */
+IWPP_API int iwpp_scan(void *marker_inout, const void *mask, int64_t H, int64_t W, int connectivity,
+                       int op, int dtype, const iwpp_plan *plan, void *workspace, size_t ws_bytes,
+                       void *stream);
+IWPP_API int iwpp_drain(void *marker_inout, const void *mask, int64_t H, int64_t W, int connectivity,
+                        int op, int dtype, const iwpp_plan *plan, void *workspace, size_t ws_bytes,
+                        void *stream);
+
+/* Waits for `stream`, then returns the device status recorded in `workspace`
+ * by the last call that used it (IWPP_OK or an iwpp_status code), or
+ * IWPP_ERR_CUDA if the stream reports an error. */
+IWPP_API int iwpp_sync_status(const void *workspace, void *stream);
+
+/*
+ * Work counters of the last single-image call that used `workspace`: tile
+ * visits by the persistent kernel, wave-queue entries processed (pops), and
+ * entries created by the visits' initial scans (seeds). Host pointer out[3].
+ * Synchronises `stream`. Returns IWPP_OK or IWPP_ERR_CUDA.
+ */
+IWPP_API int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IWPP_H */

@@ -1,0 +1,213 @@
+"""Python binding of the C ABI in include/iwpp.h (argument marshalling only).
+
+Every step of the reconstruction runs in the CUDA library ``libiwpp.so``; this
+module only passes pointers, sizes and the stream handle through ctypes. PyTorch
+is used for device memory and streams. If the library is missing, every call
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiwpp.so")
+
+IWPP_U8, IWPP_U16 = 0, 1
+IWPP_DILATE, IWPP_ERODE = 0, 1
+STATUS = {0: "IWPP_OK", 1: "IWPP_ERR_ARG", 2: "IWPP_ERR_PRECONDITION", 3: "IWPP_ERR_WORKSPACE",
+          4: "IWPP_ERR_QUEUE_FULL", 5: "IWPP_ERR_TIMEOUT", 6: "IWPP_ERR_CUDA", 7: "IWPP_ERR_INTERNAL"}
+OPS = {"dilate": IWPP_DILATE, "erode": IWPP_ERODE}
+
+
+class IwppError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)}" if what else STATUS.get(code, str(code)))
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("revisit_sweeps", ctypes.c_int32), ("smem_queue_cap", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("watchdog_ns", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+    def __repr__(self):
+        return f"Plan({self.as_dict()})"
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes) of every exported C function
+_PROTOS = [
+    ("iwpp_default_plan", ctypes.c_int, [ctypes.POINTER(Plan)]),
+    ("iwpp_tile_shape_supported", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
+    ("iwpp_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                               ctypes.POINTER(Plan)]),
+    ("iwpp_reconstruct", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_reconstruct_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(Plan), ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.c_void_p]),
+    ("iwpp_scan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Plan),
+                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_drain", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Plan),
+                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("iwpp_work_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+]
+
+
+def lib():
+    """Load libiwpp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1605_00930_gb300.build` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in _PROTOS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [p[0] for p in _PROTOS]
+
+
+# ---- thin wrappers with the C names ----------------------------------------------------
+
+def iwpp_default_plan() -> Plan:
+    p = Plan()
+    lib().iwpp_default_plan(ctypes.byref(p))
+    return p
+
+
+def iwpp_tile_shape_supported(th: int, tw: int) -> bool:
+    return bool(lib().iwpp_tile_shape_supported(th, tw))
+
+
+def iwpp_workspace_bytes(H: int, W: int, dtype: int, plan: Plan | None = None) -> int:
+    return int(lib().iwpp_workspace_bytes(H, W, dtype, ctypes.byref(plan) if plan is not None else None))
+
+
+def iwpp_reconstruct(marker_ptr, mask_ptr, H, W, conn, op, dtype, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_reconstruct(marker_ptr, mask_ptr, H, W, conn, op, dtype, ws_ptr, ws_bytes, stream)
+
+
+def iwpp_reconstruct_plan(marker_ptr, mask_ptr, H, W, conn, op, dtype, plan, ws_ptr, ws_bytes,
+                          stream) -> int:
+    return lib().iwpp_reconstruct_plan(marker_ptr, mask_ptr, H, W, conn, op, dtype,
+                                       ctypes.byref(plan) if plan is not None else None, ws_ptr,
+                                       ws_bytes, stream)
+
+
+def iwpp_scan(marker_ptr, mask_ptr, H, W, conn, op, dtype, plan, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_scan(marker_ptr, mask_ptr, H, W, conn, op, dtype,
+                           ctypes.byref(plan) if plan is not None else None, ws_ptr, ws_bytes, stream)
+
+
+def iwpp_drain(marker_ptr, mask_ptr, H, W, conn, op, dtype, plan, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_drain(marker_ptr, mask_ptr, H, W, conn, op, dtype,
+                            ctypes.byref(plan) if plan is not None else None, ws_ptr, ws_bytes, stream)
+
+
+def iwpp_sync_status(ws_ptr, stream) -> int:
+    return lib().iwpp_sync_status(ws_ptr, stream)
+
+
+def iwpp_work_counters(ws_ptr, stream):
+    out = (ctypes.c_uint64 * 3)()
+    rc = lib().iwpp_work_counters(ws_ptr, stream, out)
+    if rc != 0:
+        raise IwppError(rc, "iwpp_work_counters")
+    return {"visits": int(out[0]), "pops": int(out[1]), "seeds": int(out[2])}
+
+
+# ---- torch convenience layer -----------------------------------------------------------
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.uint8:
+        return IWPP_U8
+    if t.dtype == torch.uint16:
+        return IWPP_U16
+    raise TypeError("images must be torch.uint8 or torch.uint16")
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def alloc_workspace(nbytes: int, device=None):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+class Reconstructor:
+    """Reusable single-image reconstruction: holds a workspace sized for (H, W, dtype)."""
+
+    def __init__(self, H: int, W: int, dtype, plan: Plan | None = None, device=None):
+        import torch
+        self.H, self.W = int(H), int(W)
+        self.dtype_code = IWPP_U8 if dtype == torch.uint8 else IWPP_U16
+        self.plan = plan
+        nbytes = iwpp_workspace_bytes(self.H, self.W, self.dtype_code, plan)
+        if nbytes == 0:
+            raise IwppError(1, "iwpp_workspace_bytes")
+        self.ws = alloc_workspace(nbytes, device)
+
+    def __call__(self, marker, mask, conn: int = 8, op: str = "dilate", stream=None) -> int:
+        """Enqueue the reconstruction (in place on ``marker``); returns the host status."""
+        if marker.shape != (self.H, self.W) or mask.shape != (self.H, self.W):
+            raise ValueError("shape mismatch")
+        if _dtype_code(marker) != self.dtype_code or mask.dtype != marker.dtype:
+            raise TypeError("dtype mismatch")
+        if not (marker.is_cuda and mask.is_cuda and marker.is_contiguous() and mask.is_contiguous()):
+            raise ValueError("marker and mask must be contiguous CUDA tensors")
+        return iwpp_reconstruct_plan(ctypes.c_void_p(marker.data_ptr()), ctypes.c_void_p(mask.data_ptr()),
+                                     self.H, self.W, int(conn), OPS[op], self.dtype_code, self.plan,
+                                     ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                     _stream_handle(stream))
+
+    def phase(self, which: str, marker, mask, conn: int = 8, op: str = "dilate", stream=None) -> int:
+        """Enqueue one step of the call: which = "scan" or "drain"."""
+        fn = iwpp_scan if which == "scan" else iwpp_drain
+        return fn(ctypes.c_void_p(marker.data_ptr()), ctypes.c_void_p(mask.data_ptr()), self.H, self.W,
+                  int(conn), OPS[op], self.dtype_code, self.plan, ctypes.c_void_p(self.ws.data_ptr()),
+                  self.ws.numel(), _stream_handle(stream))
+
+    def status(self, stream=None) -> int:
+        return iwpp_sync_status(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
+
+    def counters(self, stream=None):
+        return iwpp_work_counters(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
+
+
+def reconstruct(marker, mask, conn: int = 8, op: str = "dilate", plan: Plan | None = None, stream=None):
+    """Reconstruct ``mask`` from ``marker`` in place on ``marker`` (torch CUDA tensors,
+    uint8 or uint16, contiguous 2-D). Waits for the result and raises IwppError on
+    any host- or device-side error. Returns ``marker``."""
+    R = Reconstructor(marker.shape[0], marker.shape[1], marker.dtype, plan, marker.device)
+    rc = R(marker, mask, conn, op, stream)
+    if rc != 0:
+        raise IwppError(rc, "iwpp_reconstruct")
+    st = R.status(stream)
+    if st != 0:
+        raise IwppError(st, "device status")
+    return marker

@@ -1,0 +1,92 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+function that include/iwpp.h declares; host-side argument checks reject bad
+calls before anything is enqueued (no GPU needed for these)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "iwpp.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"IWPP_API\s+[\w\s\*]+?\b(iwpp_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def iwpp():
+    if shutil.which("nvcc") is None and not os.path.exists(
+            os.path.join(ROOT, "paper_1605_00930_gb300", "libiwpp.so")):
+        pytest.skip("no nvcc and no prebuilt library")
+    from paper_1605_00930_gb300 import build
+    build.build()
+    from paper_1605_00930_gb300 import iwpp as m
+    m.lib()
+    return m
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["iwpp_reconstruct", "iwpp_reconstruct_plan", "iwpp_workspace_bytes", "iwpp_sync_status",
+              "iwpp_default_plan"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(iwpp):
+    L = iwpp.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+    # and the binding covers each one under the same name
+    assert set(_declared()) <= set(iwpp.exported_symbols())
+
+
+def test_default_plan_and_shapes(iwpp):
+    p = iwpp.iwpp_default_plan()
+    assert (p.tile_h, p.tile_w) == (64, 64)
+    assert p.sweeps >= 0 and 16 <= p.smem_queue_cap <= p.tile_h * p.tile_w
+    assert iwpp.iwpp_tile_shape_supported(64, 64)
+    assert not iwpp.iwpp_tile_shape_supported(48, 48)
+
+
+def test_host_argument_errors_return_before_any_launch(iwpp):
+    buf = (ctypes.c_uint8 * 4096)()
+    a = ctypes.addressof(buf)
+    a16 = (a + 15) // 16 * 16
+    ws = (a + 255) // 256 * 256 if a % 256 else a
+    null = ctypes.c_void_p(0)
+    P = ctypes.c_void_p
+    # null pointers
+    assert iwpp.iwpp_reconstruct(null, P(a16), 4, 4, 8, 0, 0, P(ws), 16, null) == 1
+    # misaligned image
+    assert iwpp.iwpp_reconstruct(P(a16 + 1), P(a16), 4, 4, 8, 0, 0, P(ws), 16, null) == 1
+    # bad sizes, connectivity, op, dtype
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 0, 4, 8, 0, 0, P(ws), 16, null) == 1
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 1 << 16, 1 << 16, 8, 0, 0, P(ws), 16, null) == 1
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 6, 0, 0, P(ws), 16, null) == 1
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 2, 0, P(ws), 16, null) == 1
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 3, P(ws), 16, null) == 1
+    # bad plan
+    p = iwpp.iwpp_default_plan()
+    p.tile_h = 48
+    assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
+    p = iwpp.iwpp_default_plan()
+    p.smem_queue_cap = 8
+    assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
+    # missing / misaligned workspace
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, null, 16, null) == 3
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, P(ws + 16), 16, null) == 3
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import importlib
+    from paper_1605_00930_gb300 import iwpp as m
+    mod = importlib.reload(m)
+    monkeypatch.setattr(mod, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(mod, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        mod.lib()
+    importlib.reload(m)

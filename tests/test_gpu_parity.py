@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit-exact.
+
+Reconstruction output is integer; the only acceptable difference is none. Sizes
+span several tiles with ragged tails, every tile shape and plan knob, both dtypes,
+both operators and both connectivities, plus the full-size workloads."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1605_00930_gb300 import synth
+from tests._golden import load_hand_cases
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def iw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_00930_gb300 import build
+    build.build()
+    from paper_1605_00930_gb300 import iwpp
+    iwpp.lib()
+    return iwpp
+
+
+def _tdtype(np_dtype):
+    return torch.uint8 if np.dtype(np_dtype) == np.uint8 else torch.uint16
+
+
+def gpu_run(iw, marker, mask, conn, op, plan=None, expect_status=0):
+    dt = _tdtype(marker.dtype)
+    m = torch.from_numpy(np.ascontiguousarray(marker)).cuda()
+    I = torch.from_numpy(np.ascontiguousarray(mask)).cuda()
+    R = iw.Reconstructor(marker.shape[0], marker.shape[1], dt, plan)
+    rc = R(m, I, conn, op)
+    assert rc == 0, iw.STATUS.get(rc)
+    st = R.status()
+    assert st == expect_status, iw.STATUS.get(st)
+    return m.cpu().numpy(), R
+
+
+def check(iw, oracle_lib, marker, mask, conn, op, plan=None):
+    exp = oracle_lib.reconstruct(marker, mask, conn, op)
+    got, _ = gpu_run(iw, marker, mask, conn, op, plan)
+    if not np.array_equal(got, exp):
+        bad = np.argwhere(got != exp)
+        y, x = bad[0]
+        raise AssertionError(f"{len(bad)} mismatches, first at {(y, x)}: got {got[y, x]} "
+                             f"expected {exp[y, x]} (shape {mask.shape}, conn {conn}, op {op})")
+
+
+def _plan(iw, **kw):
+    p = iw.iwpp_default_plan()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _random_pair(rng, H, W, dtype, op, vmax):
+    top = synth.maxval(dtype)
+    mask = rng.integers(0, vmax + 1, size=(H, W)).astype(dtype)
+    if op == "dilate":
+        marker = (mask.astype(np.int64) * (rng.random((H, W)) < 0.05)).astype(dtype)
+    else:
+        marker = synth.fillholes_marker(mask)
+    return marker, mask
+
+
+SHAPES = [(1, 1), (1, 700), (700, 1), (64, 64), (65, 130), (129, 65), (200, 333), (257, 513)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_random_small(iw, oracle_lib, shape, dtype, op, conn):
+    rng = np.random.default_rng([101, shape[0], shape[1], conn, op == "erode"])
+    for vmax in (7, synth.maxval(dtype)):
+        marker, mask = _random_pair(rng, *shape, dtype, op, vmax)
+        check(iw, oracle_lib, marker, mask, conn, op)
+
+
+@pytest.mark.parametrize("case", load_hand_cases(), ids=lambda c: c["name"])
+def test_hand_cases_gpu(iw, case):
+    for conn in case["conn"]:
+        got, _ = gpu_run(iw, case["marker"], case["mask"], conn, case["op"])
+        np.testing.assert_array_equal(got, case["expected"])
+
+
+@pytest.mark.parametrize("tile", [(64, 64), (32, 64), (64, 128)])
+@pytest.mark.parametrize("sweeps", [0, 1, 3])
+@pytest.mark.parametrize("qcap", [16, 1024])
+def test_plans_tissue(iw, oracle_lib, tile, sweeps, qcap):
+    c = synth.tissue_case(301, 517, nblobs=30)
+    p = _plan(iw, tile_h=tile[0], tile_w=tile[1], sweeps=sweeps, smem_queue_cap=min(qcap, tile[0] * tile[1]))
+    for conn in (4, 8):
+        check(iw, oracle_lib, c.marker, c.mask, conn, "dilate", p)
+
+
+@pytest.mark.parametrize("revisit", [0, 2])
+@pytest.mark.parametrize("bps", [0, 1])
+def test_plans_fill_holes_u16(iw, oracle_lib, revisit, bps):
+    field = synth.blob_field_u8(390, 271, 25, synth.rng_for(90))
+    mask = synth.to_u16(field)
+    p = _plan(iw, revisit_sweeps=revisit, blocks_per_sm=bps, sweeps=0)
+    check(iw, oracle_lib, synth.fillholes_marker(mask), mask, 8, "erode", p)
+
+
+def test_noise_blur_512(iw, oracle_lib):
+    c = synth.noise_blur_case()
+    check(iw, oracle_lib, c.marker, c.mask, c.conn, c.op)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_tissue_4096(iw, oracle_lib, conn):
+    c = synth.tissue_case(conn=conn)
+    check(iw, oracle_lib, c.marker, c.mask, conn, "dilate")
+
+
+def test_sparse_seeds_16384(iw, oracle_lib):
+    c = synth.sparse_seed_case()
+    check(iw, oracle_lib, c.marker, c.mask, 8, "dilate")
+
+
+def test_repeatable_output(iw, oracle_lib):
+    c = synth.tissue_case(777, 1031, nblobs=60)
+    exp = oracle_lib.reconstruct(c.marker, c.mask, 8, "dilate")
+    for _ in range(10):
+        got, _ = gpu_run(iw, c.marker, c.mask, 8, "dilate")
+        np.testing.assert_array_equal(got, exp)
+
+
+def test_precondition_violation_reported(iw):
+    mask = np.full((70, 90), 10, np.uint8)
+    marker = np.zeros_like(mask)
+    marker[33, 44] = 11
+    gpu_run(iw, marker, mask, 8, "dilate", expect_status=2)
+    up = np.full_like(mask, 10)
+    up[5, 6] = 9
+    gpu_run(iw, up, mask, 8, "erode", expect_status=2)
+
+
+def test_workspace_too_small(iw):
+    m = torch.zeros((100, 100), dtype=torch.uint8, device="cuda")
+    need = iw.iwpp_workspace_bytes(100, 100, 0)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    P = ctypes.c_void_p
+    assert iw.iwpp_reconstruct(P(m.data_ptr()), P(m.data_ptr()), 100, 100, 8, 0, 0, P(ws.data_ptr()),
+                               need - 1, s) == 3
+    assert iw.iwpp_reconstruct(P(m.data_ptr()), P(m.data_ptr()), 100, 100, 8, 0, 0, P(ws.data_ptr()),
+                               need, s) == 0
+    assert iw.iwpp_sync_status(P(ws.data_ptr()), s) == 0
+
+
+def test_watchdog_timeout_returns_and_workspace_recovers(iw, oracle_lib):
+    """A 1 ns watchdog makes an idle CTA's wait for work run out: the kernel records
+    IWPP_ERR_TIMEOUT and returns (no hang, no trap); the same workspace then serves a
+    normal call."""
+    c = synth.tissue_case(256, 1024, nblobs=40)
+    p = _plan(iw, watchdog_ns=1, sweeps=0, blocks_per_sm=1)
+    dt = torch.uint8
+    seen = set()
+    R = iw.Reconstructor(256, 1024, dt)   # workspace sized for the default plan (the larger)
+    R.plan = p
+    for _ in range(5):
+        m = torch.from_numpy(c.marker).cuda()
+        I = torch.from_numpy(c.mask).cuda()
+        assert R(m, I, 8, "dilate") == 0
+        seen.add(R.status())
+        if 5 in seen:
+            break
+    assert 5 in seen, seen
+    torch.cuda.synchronize()
+    R.plan = None
+    m = torch.from_numpy(c.marker).cuda()
+    I = torch.from_numpy(c.mask).cuda()
+    assert R(m, I, 8, "dilate") == 0
+    assert R.status() == 0
+    np.testing.assert_array_equal(m.cpu().numpy(), oracle_lib.reconstruct(c.marker, c.mask, 8, "dilate"))
+
+
+def test_work_counters(iw):
+    c = synth.tissue_case(512, 512, nblobs=20)
+    _, R = gpu_run(iw, c.marker, c.mask, 8, "dilate")
+    cnt = R.counters()
+    assert cnt["visits"] >= 1 and cnt["pops"] >= cnt["seeds"] >= 0

@@ -67,17 +67,19 @@ typedef enum {
 /*
  * Execution plan: the knobs of the propagation engine. None of them can change
  * the result (the reconstruction is unique); they change only the work done.
- *   tile_h, tile_w     tile shape; must be one of the compiled shapes
- *                      (64x64, 32x64, 64x128 — see iwpp_tile_shape_supported)
+ *   tile_h, tile_w     tile shape, one warp per tile; must be one of the
+ *                      compiled shapes (32x32, 32x64, 64x64 — see
+ *                      iwpp_tile_shape_supported)
  *   sweeps             raster + anti-raster sweep pairs run over every tile
  *                      before the queue phase (Algorithm 7's scanning phase,
  *                      tile-local); 0 = queue mode from the start
  *   revisit_sweeps     sweep pairs run at the start of every first visit of
  *                      a tile by the persistent kernel (normally 0)
  *   smem_queue_cap     entries of each of the two shared-memory wave queues
- *                      of a CTA; waves larger than this spill into the CTA's
- *                      global overflow queue (16 .. tile_h * tile_w)
- *   blocks_per_sm      persistent-kernel CTAs per SM (0 = occupancy maximum)
+ *                      of a warp; waves larger than this spill into the
+ *                      warp's global overflow queue (16 .. tile_h * tile_w)
+ *   blocks_per_sm      persistent-kernel CTAs (of 4 warps) per SM
+ *                      (0 = occupancy maximum)
  *   watchdog_ns        the persistent kernel gives up with IWPP_ERR_TIMEOUT
  *                      when a wait for work lasts longer than this
  *                      (0 = default, 10 s)
@@ -145,11 +147,12 @@ IWPP_API int iwpp_sync_status(const void *workspace, void *stream);
 
 /*
  * Work counters of the last single-image call that used `workspace`: tile
- * visits by the persistent kernel, wave-queue entries processed (pops), and
- * entries created by the visits' initial scans (seeds). Host pointer out[3].
- * Synchronises `stream`. Returns IWPP_OK or IWPP_ERR_CUDA.
+ * visits by the persistent kernel, wave-queue entries processed (pops),
+ * entries created by the visits' initial scans (seeds), wave steps run, and
+ * the persistent workers' summed waiting time and processing time in ns.
+ * Host pointer out[6]. Synchronises `stream`. Returns IWPP_OK or IWPP_ERR_CUDA.
  */
-IWPP_API int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[3]);
+IWPP_API int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[6]);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ namespace iwpp {
 struct ShapeInfo {
     int th, tw;
 };
-static const ShapeInfo kShapes[] = {{64, 64}, {32, 64}, {64, 128}};
+static const ShapeInfo kShapes[] = {{32, 32}, {32, 64}, {64, 64}};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 int shape_index(int th, int tw) {
@@ -62,9 +62,9 @@ static std::once_flag g_once;
 static std::mutex g_mu;
 
 static void init_sets() {
-    fill_shape<64, 64>(g_sets[0]);
+    fill_shape<32, 32>(g_sets[0]);
     fill_shape<32, 64>(g_sets[1]);
-    fill_shape<64, 128>(g_sets[2]);
+    fill_shape<64, 64>(g_sets[2]);
 }
 
 const KernelSet &kernels(int shape, int dtype, int conn) {
@@ -98,7 +98,7 @@ int device_sm_count() {
 }
 
 // Persistent CTAs for a plan: blocks_per_sm (or the occupancy maximum) x SMs,
-// never more than the number of tiles.
+// never more CTAs than needed to give every tile its own warp.
 int drain_grid(const iwpp_plan &p, int dtype, int conn, uint32_t ntiles) {
     const int shape = shape_index(p.tile_h, p.tile_w);
     const KernelSet &k = kernels(shape, dtype, conn);
@@ -111,7 +111,8 @@ int drain_grid(const iwpp_plan &p, int dtype, int conn, uint32_t ntiles) {
     }
     const int sms = device_sm_count();
     long long g = (long long)bps * sms;
-    if (g > (long long)ntiles) g = ntiles;
+    const long long need = ((long long)ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    if (g > need) g = need;
     return g < 1 ? 1 : (int)g;
 }
 
@@ -126,11 +127,11 @@ bool plan_valid(const iwpp_plan &p) {
 }
 
 void default_plan(iwpp_plan *p) {
-    p->tile_h = 64;
-    p->tile_w = 64;
+    p->tile_h = 32;
+    p->tile_w = 32;
     p->sweeps = 1;
     p->revisit_sweeps = 0;
-    p->smem_queue_cap = 1024;
+    p->smem_queue_cap = 512;
     p->blocks_per_sm = 0;
     p->watchdog_ns = 0;
 }
@@ -160,7 +161,7 @@ static bool make_layout(int64_t H, int64_t W, int dtype, int conn, const iwpp_pl
     L.state = 256;
     L.queue = L.state + align256((size_t)L.ntiles * 4);
     L.ovf = L.queue + align256((size_t)L.ntiles * 4);
-    L.total = L.ovf + align256((size_t)L.grid * 2 * L.ovcap * sizeof(uint16_t) + 16);
+    L.total = L.ovf + align256((size_t)L.grid * kWarpsPerCta * 2 * L.ovcap * sizeof(uint16_t) + 16);
     return true;
 }
 
@@ -214,7 +215,8 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
         if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4, stream) != cudaSuccess)
             return IWPP_ERR_CUDA;
         const int sms = device_sm_count();
-        const uint32_t scan_grid = L.ntiles < (uint32_t)(sms * 16) ? L.ntiles : (uint32_t)(sms * 16);
+        const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+        const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
         k.scan<<<scan_grid, kThreads, smem, stream>>>(a);
     }
     if (phases & kPhaseDrain) k.drain<<<L.grid, kThreads, smem, stream>>>(a);
@@ -288,7 +290,7 @@ extern "C" int iwpp_sync_status(const void *workspace, void *stream) {
     return (int)st;
 }
 
-extern "C" int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[3]) {
+extern "C" int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[6]) {
     if (!workspace || !out) return IWPP_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     iwpp::WsHeader h;
@@ -298,5 +300,8 @@ extern "C" int iwpp_work_counters(const void *workspace, void *stream, uint64_t 
     out[0] = h.visits;
     out[1] = h.pops;
     out[2] = h.seeds;
+    out[3] = h.waves;
+    out[4] = h.idle_ns;
+    out[5] = h.busy_ns;
     return IWPP_OK;
 }

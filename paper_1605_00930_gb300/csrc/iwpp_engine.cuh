@@ -9,20 +9,23 @@
 // is loaded into shared memory and undone when it is stored.
 //
 // GB300 design (not the paper's Xeon Phi / Kepler design):
-//   * The image is cut into TH x TW tiles; a tile is the unit of work. A CTA
-//     holds one tile plus a one-pixel halo in shared memory, widened to 32-bit
-//     words so that propagation can use native shared-memory atomicMax.
+//   * The image is cut into TH x TW tiles; a tile is the unit of work. Each WARP
+//     is an independent worker that holds one tile plus a one-pixel halo in its
+//     own slice of shared memory (J widened to 32-bit words so that propagation
+//     can use native shared-memory atomicMax; I as 16-bit words). A serial wave
+//     chain inside a tile then costs warp-level synchronisation only, and an SM
+//     keeps a dozen or more tiles in flight to hide the latency of each chain.
 //     Tiles move between HBM and shared memory in 16-byte chunks.
-//   * Tile-local scanning (Algorithm 7's raster / anti-raster sweeps): each warp
-//     sweeps a band of rows; within a row the left-to-right dependency
+//   * Tile-local scanning (Algorithm 7's raster / anti-raster sweeps): rows in
+//     order; within a row the left-to-right dependency
 //     J(x) = min(I(x), max(a(x), J(x-1))) is a composition of clamp functions,
 //     which is associative, so it runs as a warp-shuffle scan.
 //   * Tile-local irregular propagation (Algorithm 7's queue phase; the in/out
 //     queue pair of Algorithm 9 and Sec. 4.1): double-buffered shared-memory
 //     wave queues with a per-pixel "queued" bitmap, warp-aggregated pushes (one
-//     shared atomicAdd per warp and wave step), shared atomicMax updates with
-//     re-enqueue on change, and a per-CTA global overflow queue for waves larger
-//     than the shared one.
+//     ballot per direction and a single count update per warp and wave step),
+//     shared atomicMax updates with re-enqueue on change, and a per-warp global
+//     overflow queue for waves larger than the shared one.
 //   * Cross-tile propagation: a tile only ever writes its own pixels. When a
 //     tile's edge pixels can raise a halo pixel, the owning neighbour tile is
 //     notified. A per-tile state word (PENDING / ACTIVE / VISITED) guarantees
@@ -40,6 +43,17 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+// Tuning switches (compile-time; the defaults are the measured best).
+#ifndef IWPP_DRAIN_MINB
+#define IWPP_DRAIN_MINB 4     // persistent-kernel CTAs per SM the register budget targets
+#endif
+#ifndef IWPP_PHASE_TIMING
+#define IWPP_PHASE_TIMING 0   // accumulate per-phase SM cycles of the persistent kernel
+#endif
+#ifndef IWPP_BACKOFF_MAX
+#define IWPP_BACKOFF_MAX 512  // ns, longest sleep between polls of an empty queue slot
+#endif
+
 namespace iwpp {
 
 // ---- status codes (mirror iwpp_status in include/iwpp.h) ------------------------------
@@ -52,8 +66,8 @@ enum : uint32_t {
 enum : uint32_t { ST_PENDING = 1u, ST_ACTIVE = 2u, ST_VISITED = 4u };
 constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;
 constexpr uint32_t kDone = 0xFFFFFFFFu;
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kWarpsPerCta = 4;                 // independent tile workers per CTA
+constexpr int kThreads = 32 * kWarpsPerCta;
 
 // Workspace header, at offset 0 of the workspace (256 bytes reserved).
 struct WsHeader {
@@ -65,6 +79,12 @@ struct WsHeader {
     unsigned long long visits;  // tile visits by the persistent kernel
     unsigned long long pops;    // wave-queue entries processed
     unsigned long long seeds;   // wave-queue entries created by a visit's initial scan
+    unsigned long long waves;   // wave steps run by the persistent kernel
+    unsigned long long idle_ns; // summed over warps: time spent waiting for a tile
+    unsigned long long busy_ns; // summed over warps: time spent processing tiles
+    unsigned int max_gen;       // longest chain of tile visits that notified one another
+    unsigned int pad1;
+    unsigned long long phase_cycles[8];  // IWPP_PHASE_TIMING builds only
 };
 static_assert(sizeof(WsHeader) <= 256, "header too large");
 
@@ -83,10 +103,10 @@ struct EngineArgs {
     WsHeader *hdr;
     uint32_t *state;    // ntiles words
     uint32_t *queue;    // ntiles slots
-    uint16_t *ovf;      // per-CTA overflow queues, 2 * ovcap entries each
+    uint16_t *ovf;      // per-warp overflow queues, 2 * ovcap entries each
     uint32_t ntiles;
     uint32_t qcap;      // shared wave-queue entries per buffer
-    uint32_t ovcap;     // global overflow entries per buffer per CTA
+    uint32_t ovcap;     // global overflow entries per buffer per warp
     int sweeps;         // sweep pairs in the scan kernel
     int revisit_sweeps; // sweep pairs at a tile's first persistent visit
     long long watchdog_ns;
@@ -145,6 +165,7 @@ __device__ inline uint32_t pop_tile(const EngineArgs &a) {
     const unsigned long long ticket = atomicAdd(&a.hdr->head, 1ull);
     uint32_t *slot = a.queue + (ticket % a.ntiles);
     const unsigned long long t0 = globaltimer_ns();
+    unsigned int backoff = 32;
     for (;;) {
         const uint32_t v = ld_volatile(slot);
         if (v != kEmptySlot && atomicCAS(slot, v, kEmptySlot) == v) return v;
@@ -154,207 +175,247 @@ __device__ inline uint32_t pop_tile(const EngineArgs &a) {
             set_status(a.hdr, kErrTimeout);
             return kDone;
         }
-        __nanosleep(64);
+        __nanosleep(backoff);
+        if (backoff < IWPP_BACKOFF_MAX) backoff <<= 1;
     }
 }
 
-// ---- the tile engine -----------------------------------------------------------------------
+// ---- the tile engine (one warp per tile) ------------------------------------------------------
+// Shared-memory words of J hold (value << 1) | queued. A pop is one atomicAnd that clears
+// the queued flag and returns the newest value; a raise is one atomicMax with the flag
+// set, whose old word says whether the pixel must be queued (flag was clear). So a raise
+// that lands after a pop re-queues the pixel, and none is lost, without fences. Halo
+// words keep the flag set: the tile may raise its copies of halo pixels (that is how it
+// finds improvements to send to the neighbours) but never queues them.
 template <typename T, int CONN, int TH, int TW>
 struct Tile {
-    static_assert(TW % 32 == 0 && TH % kWarps == 0 && TH >= 8, "tile shape");
-    static constexpr int PW = TW + 2;                     // padded row length
+    static_assert(TW % 32 == 0 && TH >= 4 && TH <= 64, "tile shape");
+    static constexpr int XOFF = 4;                        // padded column of image column x0
+    static constexpr int PW = TW + 8;                     // padded row length (16-byte rows)
     static constexpr int PH = TH + 2;
     static constexpr int NP = PW * PH;                    // padded pixels
     static constexpr int NPIX = TH * TW;                  // owned pixels
     static constexpr int PPL = TW / 32;                   // pixels per lane in a sweep row
-    static constexpr int BAND = TH / kWarps;              // rows per warp in a sweep
     static constexpr int NRING = 2 * TW + 2 * (TH - 2);   // owned pixels on the tile edge
-    static constexpr int NHALO = 2 * PW + 2 * TH;         // halo pixels
+    static constexpr int NHALO = 2 * (TW + 2) + 2 * TH;   // halo pixels
     static constexpr int S = (int)sizeof(T);
     static constexpr int EPC = 16 / S;                    // elements per 16-byte chunk
-    static constexpr int LCHUNKS = (PW * S + 15) / 16 + 1;  // chunks per loaded row
-    static constexpr int SCHUNKS = (TW * S + 15) / 16 + 1;  // chunks per stored row
-    static constexpr int INQ_WORDS = (NP + 31) / 32;
+    static constexpr int ICH = TW / EPC + 1;              // chunks covering TW elements at any alignment
+    static constexpr int NITEMS = PH * ICH;               // chunk slots of one loaded array
+    static constexpr size_t STAGE_BYTES = (size_t)2 * NITEMS * 16;
     static constexpr int NDIR = CONN;
+    static constexpr uint32_t QBIT = 1u;
     static_assert(NP < 65536, "queue entries are 16-bit padded indices");
 
     struct Smem {
-        uint32_t *J;        // NP: marker/result in the dilation domain
-        uint32_t *I;        // NP: mask; 0 on the halo and outside the image (blocks updates)
-        uint32_t *haloI;    // NHALO: real mask values of the halo (for notifications)
-        uint32_t *ring0;    // NRING: edge values at the start of the visit
-        uint32_t *inq;      // INQ_WORDS: "pixel is queued" bitmap
-        uint32_t *misc;     // 32 counters / flags
-        uint8_t *rowchg;    // TH: row changed in this visit
-        uint16_t *q;        // 2 * qcap: wave queues
+        uint32_t *J;        // NP words: (value << 1) | queued, dilation domain
+        uint16_t *I;        // NP: mask (dilation domain); 0 outside the image
+        uint32_t *halo0;    // NHALO: halo values when they were loaded
+        uint32_t *misc;     // 32 flags
+        uint16_t *q;        // 2 * qcap: wave queues ...
+        uint8_t *stage;     // ... whose space doubles as the staging area of a tile load
     };
-    // misc word indices
-    enum { M_QN = 0 /* 0..2 */, M_NOTIFY = 3 /* 3..11 */, M_FLAG = 12, M_TILE = 13, M_FIRST = 14,
-           M_REDO = 15, M_SEEDS = 16, M_PRECOND = 17 };
+    enum { M_NOTIFY = 0 /* 0..8 */, M_PRECOND = 9 };
 
-    static size_t smem_bytes(uint32_t qcap) {
-        return (size_t)(2 * NP + NHALO + NRING + INQ_WORDS + 32) * 4 + (size_t)((TH + 3) / 4) * 4 +
-               (size_t)qcap * 2 * 2;
+    static __host__ __device__ constexpr size_t words_fixed() {
+        return ((size_t)NP + (NP + 1) / 2 + NHALO + 32 + 3) & ~(size_t)3;
     }
+    static __host__ __device__ size_t qbytes(uint32_t qcap) {
+        const size_t b = (size_t)qcap * 2 * 2;
+        return ((b > STAGE_BYTES ? b : STAGE_BYTES) + 15) & ~(size_t)15;
+    }
+    // Shared memory of one warp (a 16-byte multiple, so that slices stay aligned).
+    static __host__ __device__ size_t smem_per_warp(uint32_t qcap) { return words_fixed() * 4 + qbytes(qcap); }
+    static size_t smem_bytes(uint32_t qcap) { return smem_per_warp(qcap) * kWarpsPerCta; }
 
     static __device__ Smem carve(uint8_t *base) {
         Smem s;
         uint32_t *w = reinterpret_cast<uint32_t *>(base);
         s.J = w; w += NP;
-        s.I = w; w += NP;
-        s.haloI = w; w += NHALO;
-        s.ring0 = w; w += NRING;
-        s.inq = w; w += INQ_WORDS;
-        s.misc = w; w += 32;
-        s.rowchg = reinterpret_cast<uint8_t *>(w); w += (TH + 3) / 4;
+        s.I = reinterpret_cast<uint16_t *>(w); w += (NP + 1) / 2;
+        s.halo0 = w; w += NHALO;
+        s.misc = w;
+        w = reinterpret_cast<uint32_t *>(base) + words_fixed();
         s.q = reinterpret_cast<uint16_t *>(w);
+        s.stage = reinterpret_cast<uint8_t *>(w);
         return s;
     }
 
-    // Ring position i in [0, NRING) -> padded (row, col) of an owned edge pixel.
+    // padded index of padded row r (0 = top halo) and tile column c (-1 = left halo)
+    static __device__ __forceinline__ int pidx(int r, int c) { return r * PW + XOFF + c; }
+    // Ring position i in [0, NRING) -> (padded row, tile column) of an owned edge pixel.
     static __device__ __forceinline__ void ring_rc(int i, int &r, int &c) {
-        if (i < TW) { r = 1; c = 1 + i; }
-        else if (i < 2 * TW) { r = TH; c = 1 + (i - TW); }
-        else if (i < 2 * TW + (TH - 2)) { r = 2 + (i - 2 * TW); c = 1; }
-        else { r = 2 + (i - 2 * TW - (TH - 2)); c = TW; }
+        if (i < TW) { r = 1; c = i; }
+        else if (i < 2 * TW) { r = TH; c = i - TW; }
+        else if (i < 2 * TW + (TH - 2)) { r = 2 + (i - 2 * TW); c = 0; }
+        else { r = 2 + (i - 2 * TW - (TH - 2)); c = TW - 1; }
     }
-    // Halo pixel (padded r, c on the outer ring) -> haloI index.
-    static __device__ __forceinline__ int halo_index(int r, int c) {
-        if (r == 0) return c;
-        if (r == PH - 1) return PW + c;
-        if (c == 0) return 2 * PW + (r - 1);
-        return 2 * PW + TH + (r - 1);
-    }
-    static __device__ __forceinline__ bool is_halo(int r, int c) {
-        return r == 0 || r == PH - 1 || c == 0 || c == PW - 1;
+    // Halo position i in [0, NHALO) -> (padded row, tile column).
+    static __device__ __forceinline__ void halo_rc(int i, int &r, int &c) {
+        if (i < TW + 2) { r = 0; c = i - 1; }
+        else if (i < 2 * (TW + 2)) { r = PH - 1; c = i - (TW + 2) - 1; }
+        else if (i < 2 * (TW + 2) + TH) { r = 1 + (i - 2 * (TW + 2)); c = -1; }
+        else { r = 1 + (i - 2 * (TW + 2) - TH); c = TW; }
     }
     static __device__ __forceinline__ int dir_dy(int d) {
         if (CONN == 8) return d < 3 ? -1 : (d < 5 ? 0 : 1);
         return d == 0 ? -1 : (d == 3 ? 1 : 0);
     }
     static __device__ __forceinline__ int dir_dx(int d) {
-        if (CONN == 8) { const int t[8] = {-1, 0, 1, -1, 1, -1, 0, 1}; return t[d]; }
-        const int t[4] = {0, -1, 1, 0};
-        return t[d];
+        if (CONN == 8) return (d == 0 || d == 3 || d == 5) ? -1 : ((d == 2 || d == 4 || d == 7) ? 1 : 0);
+        return d == 1 ? -1 : (d == 2 ? 1 : 0);
     }
     static __device__ __forceinline__ int nb_off(int d) { return dir_dy(d) * PW + dir_dx(d); }
     static __device__ __forceinline__ uint32_t to_dom(uint32_t v, uint32_t flip) { return v ^ flip; }
+    static __device__ __forceinline__ uint32_t val(uint32_t w) { return w >> 1; }
 
-    // ---- HBM <-> shared memory ------------------------------------------------------------
-    // Load padded rows [r0, r0 + rows) of tile (ty, tx): J and/or I, in 16-byte chunks.
-    // Elements outside the image are left alone (zero_outside covers them). Halo mask
-    // values go to haloI while I keeps 0 on the halo. use_cg: read J through L2 only
-    // (the persistent kernel reads pixels that other CTAs write concurrently).
-    static __device__ void load_rows(const ImageView &im, const Smem &s, int ty, int tx, int r0,
-                                     int rows, bool loadJ, bool loadI, bool use_cg) {
+    static __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+    }
+
+    // ---- HBM -> shared memory (all 32 lanes of the warp) ---------------------------------
+    // Loads tile (ty, tx) with its one-pixel halo. Every full 16-byte chunk that covers the
+    // tile's own columns of a padded row is copied into the staging area with cp.async (all
+    // in flight at once, through L2 only so that J written by other warps is seen), then
+    // widened; the two halo columns are read element by element. Positions outside the image
+    // get J = flag only (value 0) and I = 0, so they can never be raised or queued. Halo
+    // words carry the queued flag; halo0 keeps the halo values.
+    static __device__ void load_tile(const ImageView &im, const Smem &s, int ty, int tx, int lane) {
         const int y0 = ty * TH, x0 = tx * TW;
         const size_t total = (size_t)im.H * (size_t)im.W;
-        const int nitems = rows * LCHUNKS;
-        for (int it = threadIdx.x; it < nitems; it += kThreads) {
-            const int r = r0 + it / LCHUNKS, k = it % LCHUNKS;
+        const int xe = min(im.W, x0 + TW);             // end of the tile's own columns
+        uint8_t *stJ = s.stage, *stI = s.stage + NITEMS * 16;
+        // fill everything that may stick out of the image first
+        if (y0 == 0 || x0 == 0 || y0 + TH >= im.H || x0 + TW >= im.W) {
+            for (int p = lane; p < NP; p += 32) { s.J[p] = QBIT; s.I[p] = 0; }
+            __syncwarp();
+        }
+        for (int it = lane; it < NITEMS; it += 32) {
+            const int r = it / ICH, k = it % ICH;
             const int gy = y0 + r - 1;
             if (gy < 0 || gy >= im.H) continue;
-            const int xa = max(0, x0 - 1), xb = min(im.W, x0 + TW + 1);
             const size_t rowbase = (size_t)gy * im.W;
-            const size_t e_lo = rowbase + xa, e_hi = rowbase + xb;
-            const size_t chunk = e_lo / EPC + k;
-            if (chunk * EPC >= e_hi) continue;
+            const size_t chunk = (rowbase + x0) / EPC + k;
+            if (chunk * EPC >= rowbase + xe || (chunk + 1) * EPC > total) continue;
+            cp_async16(stJ + it * 16, reinterpret_cast<const uint4 *>(im.J) + chunk);
+            cp_async16(stI + it * 16, reinterpret_cast<const uint4 *>(im.I) + chunk);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        // the two halo columns, element by element, while the copies are in flight
+        for (int i = lane; i < 2 * PH; i += 32) {
+            const int r = i >> 1, c = (i & 1) ? TW : -1;
+            const int gy = y0 + r - 1, gx = x0 + c;
+            if (gy < 0 || gy >= im.H || gx < 0 || gx >= im.W) continue;
+            const size_t e = (size_t)gy * im.W + gx;
+            const uint32_t jv = to_dom(__ldcg(reinterpret_cast<const T *>(im.J) + e), im.flip);
+            const uint32_t iv = to_dom(reinterpret_cast<const T *>(im.I)[e], im.flip);
+            s.J[pidx(r, c)] = (jv << 1) | QBIT;
+            s.I[pidx(r, c)] = (uint16_t)iv;
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncwarp();
+        for (int it = lane; it < NITEMS; it += 32) {
+            const int r = it / ICH, k = it % ICH;
+            const int gy = y0 + r - 1;
+            if (gy < 0 || gy >= im.H) continue;
+            const size_t rowbase = (size_t)gy * im.W;
+            const size_t lo = rowbase + x0, hi = rowbase + xe;
+            const size_t chunk = lo / EPC + k;
             const size_t e0 = chunk * EPC;
+            if (e0 >= hi) continue;
+            const uint32_t hflag = (r == 0 || r == PH - 1) ? QBIT : 0u;
             union { uint4 u; T e[EPC]; } vj, vi;
             if (e0 + EPC <= total) {
-                if (loadJ) vj.u = use_cg ? __ldcg(reinterpret_cast<const uint4 *>(im.J) + chunk)
-                                         : reinterpret_cast<const uint4 *>(im.J)[chunk];
-                if (loadI) vi.u = __ldg(reinterpret_cast<const uint4 *>(im.I) + chunk);
+                vj.u = *reinterpret_cast<const uint4 *>(stJ + it * 16);
+                vi.u = *reinterpret_cast<const uint4 *>(stI + it * 16);
             } else {
 #pragma unroll
                 for (int j = 0; j < EPC; j++) {
                     if (e0 + j < total) {
-                        if (loadJ) vj.e[j] = use_cg ? __ldcg(reinterpret_cast<const T *>(im.J) + e0 + j)
-                                                    : reinterpret_cast<const T *>(im.J)[e0 + j];
-                        if (loadI) vi.e[j] = reinterpret_cast<const T *>(im.I)[e0 + j];
+                        vj.e[j] = __ldcg(reinterpret_cast<const T *>(im.J) + e0 + j);
+                        vi.e[j] = reinterpret_cast<const T *>(im.I)[e0 + j];
                     }
                 }
             }
+            uint32_t *jrow = s.J + pidx(r, 0) - (int)(lo - rowbase);   // jrow[x - rowbase... ] see below
+            uint16_t *irow = s.I + pidx(r, 0) - (int)(lo - rowbase);
+            // element e of the image row sits at column (e - lo) of the tile
+            const int base = (int)((int64_t)e0 - (int64_t)rowbase);    // image column of element 0
+            if (e0 >= lo && e0 + EPC <= hi) {
 #pragma unroll
-            for (int j = 0; j < EPC; j++) {
-                const size_t e = e0 + j;
-                if (e < e_lo || e >= e_hi) continue;
-                const int c = (int)(e - rowbase) - x0 + 1;
-                const int p = r * PW + c;
-                if (loadJ) s.J[p] = to_dom(vj.e[j], im.flip);
-                if (loadI) {
-                    const uint32_t iv = to_dom(vi.e[j], im.flip);
-                    if (is_halo(r, c)) { s.haloI[halo_index(r, c)] = iv; s.I[p] = 0; }
-                    else s.I[p] = iv;
+                for (int j = 0; j < EPC; j++) {
+                    jrow[base + j] = (to_dom(vj.e[j], im.flip) << 1) | hflag;
+                    irow[base + j] = (uint16_t)to_dom(vi.e[j], im.flip);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < EPC; j++) {
+                    const size_t e = e0 + j;
+                    if (e < lo || e >= hi) continue;
+                    jrow[base + j] = (to_dom(vj.e[j], im.flip) << 1) | hflag;
+                    irow[base + j] = (uint16_t)to_dom(vi.e[j], im.flip);
                 }
             }
         }
+        __syncwarp();
     }
 
-    // Zero J and/or I (and haloI) where the padded tile sticks out of the image.
-    static __device__ void zero_outside(const ImageView &im, const Smem &s, int ty, int tx,
-                                        bool doJ, bool doI) {
-        const int y0 = ty * TH, x0 = tx * TW;
-        if (y0 > 0 && x0 > 0 && y0 + TH < im.H && x0 + TW < im.W) return;
-        for (int p = threadIdx.x; p < NP; p += kThreads) {
-            const int r = p / PW, c = p % PW;
-            const int gy = y0 + r - 1, gx = x0 + c - 1;
-            if (gy < 0 || gy >= im.H || gx < 0 || gx >= im.W) {
-                if (doJ) s.J[p] = 0;
-                if (doI) {
-                    s.I[p] = 0;
-                    if (is_halo(r, c)) s.haloI[halo_index(r, c)] = 0;
-                }
-            }
-        }
-    }
-
-    // Reload the halo ring of J (the interior stays as this CTA left it).
-    static __device__ void load_halo_J(const ImageView &im, const Smem &s, int ty, int tx) {
-        const int y0 = ty * TH, x0 = tx * TW;
-        for (int i = threadIdx.x; i < NHALO; i += kThreads) {
+    // Remember the halo values (after a load or a halo reload).
+    static __device__ void save_halo(const Smem &s, int lane) {
+        for (int i = lane; i < NHALO; i += 32) {
             int r, c;
-            if (i < PW) { r = 0; c = i; }
-            else if (i < 2 * PW) { r = PH - 1; c = i - PW; }
-            else if (i < 2 * PW + TH) { r = 1 + (i - 2 * PW); c = 0; }
-            else { r = 1 + (i - 2 * PW - TH); c = PW - 1; }
-            const int gy = y0 + r - 1, gx = x0 + c - 1;
-            uint32_t v = 0;
-            if (gy >= 0 && gy < im.H && gx >= 0 && gx < im.W)
-                v = to_dom(__ldcg(reinterpret_cast<const T *>(im.J) + (size_t)gy * im.W + gx), im.flip);
-            s.J[r * PW + c] = v;
+            halo_rc(i, r, c);
+            s.halo0[i] = val(s.J[pidx(r, c)]);
         }
     }
 
-    // Store the owned rows flagged in rowchg, in 16-byte chunks where a chunk lies
+    // Reload the halo ring of J (the interior stays as this warp left it).
+    static __device__ void load_halo_J(const ImageView &im, const Smem &s, int ty, int tx, int lane) {
+        const int y0 = ty * TH, x0 = tx * TW;
+        for (int i = lane; i < NHALO; i += 32) {
+            int r, c;
+            halo_rc(i, r, c);
+            const int gy = y0 + r - 1, gx = x0 + c;
+            uint32_t w = QBIT;
+            if (gy >= 0 && gy < im.H && gx >= 0 && gx < im.W)
+                w = (to_dom(__ldcg(reinterpret_cast<const T *>(im.J) + (size_t)gy * im.W + gx), im.flip) << 1) | QBIT;
+            s.J[pidx(r, c)] = w;
+        }
+        __syncwarp();
+    }
+
+    // Store the owned rows whose bit is set in rowmask, in 16-byte chunks where a chunk lies
     // entirely inside the tile's row segment, element by element otherwise.
-    static __device__ void store_rows(const ImageView &im, const Smem &s, int ty, int tx, bool use_cg) {
+    static __device__ void store_tile(const ImageView &im, const Smem &s, int ty, int tx,
+                                      unsigned long long rowmask, bool use_cg, int lane) {
         const int y0 = ty * TH, x0 = tx * TW;
         const size_t total = (size_t)im.H * (size_t)im.W;
-        const int nitems = TH * SCHUNKS;
-        for (int it = threadIdx.x; it < nitems; it += kThreads) {
-            const int rr = it / SCHUNKS, k = it % SCHUNKS;
-            if (!s.rowchg[rr]) continue;
+        const int xe = min(im.W, x0 + TW);
+        for (int it = lane; it < TH * ICH; it += 32) {
+            const int rr = it / ICH, k = it % ICH;
+            if (!((rowmask >> rr) & 1ull)) continue;
             const int gy = y0 + rr;
             if (gy >= im.H) continue;
             const size_t rowbase = (size_t)gy * im.W;
-            const size_t e_lo = rowbase + x0, e_hi = rowbase + min(im.W, x0 + TW);
-            const size_t chunk = e_lo / EPC + k;
-            if (chunk * EPC >= e_hi) continue;
+            const size_t lo = rowbase + x0, hi = rowbase + xe;
+            const size_t chunk = lo / EPC + k;
             const size_t e0 = chunk * EPC;
-            const uint32_t *srow = s.J + (rr + 1) * PW + 1 - x0;   // srow[x] = padded pixel at column x
-            if (e0 >= e_lo && e0 + EPC <= e_hi && e0 + EPC <= total) {
+            if (e0 >= hi) continue;
+            const uint32_t *jrow = s.J + pidx(rr + 1, 0) - (int)(lo - rowbase);
+            const int base = (int)((int64_t)e0 - (int64_t)rowbase);
+            if (e0 >= lo && e0 + EPC <= hi && e0 + EPC <= total) {
                 union { uint4 u; T e[EPC]; } v;
 #pragma unroll
-                for (int j = 0; j < EPC; j++) v.e[j] = (T)to_dom(srow[(int)(e0 + j - rowbase)], im.flip);
+                for (int j = 0; j < EPC; j++) v.e[j] = (T)to_dom(val(jrow[base + j]), im.flip);
                 if (use_cg) __stcg(reinterpret_cast<uint4 *>(im.J) + chunk, v.u);
                 else reinterpret_cast<uint4 *>(im.J)[chunk] = v.u;
             } else {
 #pragma unroll
                 for (int j = 0; j < EPC; j++) {
                     const size_t e = e0 + j;
-                    if (e < e_lo || e >= e_hi) continue;
-                    const T v = (T)to_dom(srow[(int)(e - rowbase)], im.flip);
+                    if (e < lo || e >= hi) continue;
+                    const T v = (T)to_dom(val(jrow[base + j]), im.flip);
                     if (use_cg) __stcg(reinterpret_cast<T *>(im.J) + e, v);
                     else reinterpret_cast<T *>(im.J)[e] = v;
                 }
@@ -365,20 +426,21 @@ struct Tile {
     // ---- tile-local sweeps (Algorithm 7, scanning phase) -------------------------------------
     // The clamp f(x) = min(hi, max(lo, x)) is packed as (hi << 16) | lo; values are < 2^16.
     // Composition g o f of clamps [lf, hf] then [lg, hg] is [clamp(lf, lg, hg), clamp(hf, lg, hg)].
+    // Sweeps run before any pixel is queued, on the values; they return a mask of the rows
+    // they changed.
 
     // Raster: rows top to bottom, J(p) <- max{J(q): q in N+(p) U {p}} ^ I(p) with
-    // N+ = {N, W} (4-conn) or {NW, N, NE, W} (8-conn); each warp owns BAND rows.
-    static __device__ void sweep_raster(const Smem &s) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int b = 0; b < BAND; b++) {
-            const int r = 1 + warp * BAND + b;
+    // N+ = {N, W} (4-conn) or {NW, N, NE, W} (8-conn).
+    static __device__ unsigned long long sweep_raster(const Smem &s, int lane) {
+        unsigned long long chg = 0;
+        for (int r = 1; r <= TH; r++) {
             uint32_t a[PPL], iv[PPL], old[PPL];
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                const int p = r * PW + 1 + lane * PPL + k;
-                old[k] = s.J[p];
-                uint32_t v = max(old[k], s.J[p - PW]);
-                if (CONN == 8) v = max(v, max(s.J[p - PW - 1], s.J[p - PW + 1]));
+                const int p = pidx(r, lane * PPL + k);
+                old[k] = val(s.J[p]);
+                uint32_t v = max(old[k], val(s.J[p - PW]));
+                if (CONN == 8) v = max(v, max(val(s.J[p - PW - 1]), val(s.J[p - PW + 1])));
                 a[k] = v;
                 iv[k] = s.I[p];
             }
@@ -398,32 +460,32 @@ struct Tile {
                 }
             }
             const uint32_t ex = __shfl_up_sync(0xffffffffu, (hi << 16) | lo, 1);
-            uint32_t x = s.J[r * PW];                     // left halo
+            uint32_t x = val(s.J[pidx(r, -1)]);           // left halo
             if (lane > 0) x = clampu(x, ex & 0xffffu, ex >> 16);
             bool ch = false;
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
                 x = clampu(x, min(a[k], iv[k]), iv[k]);
-                s.J[r * PW + 1 + lane * PPL + k] = x;
+                s.J[pidx(r, lane * PPL + k)] = x << 1;
                 ch |= (x != old[k]);
             }
-            if (__any_sync(0xffffffffu, ch) && lane == 0) s.rowchg[r - 1] = 1;
+            if (__any_sync(0xffffffffu, ch)) chg |= 1ull << (r - 1);
             __syncwarp();
         }
+        return chg;
     }
 
     // Anti-raster: rows bottom to top, right to left, with N- = {S, E} / {SE, S, SW, E}.
-    static __device__ void sweep_antiraster(const Smem &s) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int b = BAND - 1; b >= 0; b--) {
-            const int r = 1 + warp * BAND + b;
+    static __device__ unsigned long long sweep_antiraster(const Smem &s, int lane) {
+        unsigned long long chg = 0;
+        for (int r = TH; r >= 1; r--) {
             uint32_t a[PPL], iv[PPL], old[PPL];
 #pragma unroll
             for (int k = 0; k < PPL; k++) {
-                const int p = r * PW + 1 + lane * PPL + k;
-                old[k] = s.J[p];
-                uint32_t v = max(old[k], s.J[p + PW]);
-                if (CONN == 8) v = max(v, max(s.J[p + PW - 1], s.J[p + PW + 1]));
+                const int p = pidx(r, lane * PPL + k);
+                old[k] = val(s.J[p]);
+                uint32_t v = max(old[k], val(s.J[p + PW]));
+                if (CONN == 8) v = max(v, max(val(s.J[p + PW - 1]), val(s.J[p + PW + 1])));
                 a[k] = v;
                 iv[k] = s.I[p];
             }
@@ -443,300 +505,306 @@ struct Tile {
                 }
             }
             const uint32_t ex = __shfl_down_sync(0xffffffffu, (hi << 16) | lo, 1);
-            uint32_t x = s.J[r * PW + PW - 1];            // right halo
+            uint32_t x = val(s.J[pidx(r, TW)]);           // right halo
             if (lane < 31) x = clampu(x, ex & 0xffffu, ex >> 16);
             bool ch = false;
 #pragma unroll
             for (int k = PPL - 1; k >= 0; k--) {
                 x = clampu(x, min(a[k], iv[k]), iv[k]);
-                s.J[r * PW + 1 + lane * PPL + k] = x;
+                s.J[pidx(r, lane * PPL + k)] = x << 1;
                 ch |= (x != old[k]);
             }
-            if (__any_sync(0xffffffffu, ch) && lane == 0) s.rowchg[r - 1] = 1;
+            if (__any_sync(0xffffffffu, ch)) chg |= 1ull << (r - 1);
             __syncwarp();
         }
+        return chg;
     }
 
-    // ---- wave queues ------------------------------------------------------------------------
-    // Warp-aggregated push of up to K candidates per lane into wave buffer `buf`
-    // (count word misc[M_QN + cnt]): one shared atomicAdd per warp.
+    // ---- wave queues (private to the warp) ------------------------------------------------------
+    // Warp-aggregated push: every lane holds a bitmask of up to K candidates; a warp
+    // exclusive prefix sum of the per-lane counts gives each lane its slots. The count is a
+    // warp-uniform register (the queues belong to one warp).
     template <int K>
-    static __device__ __forceinline__ void push_warp(const Smem &s, const EngineArgs &a,
-                                                     uint16_t *ovf, int buf, int cnt,
-                                                     const bool (&w)[K], const int (&q)[K]) {
-        const int lane = threadIdx.x & 31;
-        uint32_t bal[K];
-        uint32_t total = 0;
+    static __device__ __forceinline__ void push_warp(const Smem &s, const EngineArgs &a, uint16_t *ovf,
+                                                     int buf, uint32_t &cnt, uint32_t cm,
+                                                     const int (&q)[K], int lane) {
+        const uint32_t mine = __popc(cm);
+        uint32_t incl = mine;
 #pragma unroll
-        for (int d = 0; d < K; d++) { bal[d] = __ballot_sync(0xffffffffu, w[d]); total += __popc(bal[d]); }
-        if (total == 0) return;
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(&s.misc[M_QN + cnt], total);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const uint32_t lt = (1u << lane) - 1u;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t pos = cnt + incl - mine;
 #pragma unroll
         for (int d = 0; d < K; d++) {
-            if (w[d]) {
-                const uint32_t pos = base + __popc(bal[d] & lt);
+            if ((cm >> d) & 1u) {
                 if (pos < a.qcap) s.q[buf * a.qcap + pos] = (uint16_t)q[d];
                 else if (pos - a.qcap < a.ovcap) ovf[buf * a.ovcap + (pos - a.qcap)] = (uint16_t)q[d];
                 else set_status(a.hdr, kErrQueueFull);
+                pos++;
             }
-            base += __popc(bal[d]);
         }
+        cnt += total;
     }
 
-    // Receiver test at one owned pixel p: raise it to min(I(p), max of its
-    // neighbours) if that is larger (one Jacobi step of Eq. "recon"), and queue it.
-    static __device__ __forceinline__ bool seed_pixel(const Smem &s, int p) {
-        uint32_t m = 0;
-#pragma unroll
-        for (int d = 0; d < NDIR; d++) m = max(m, s.J[p + nb_off(d)]);
-        const uint32_t nv = min(m, s.I[p]);
-        if (nv > s.J[p]) {
-            s.J[p] = nv;
-            s.rowchg[p / PW - 1] = 1;
-            return true;
-        }
-        return false;
+    static __device__ __forceinline__ void mark_row(unsigned long long &rows, int q) {
+        const int r = q / PW;
+        if (r >= 1 && r <= TH) rows |= 1ull << (r - 1);
     }
 
-    // Initial wave of a visit. full: every owned pixel is tested (first visit);
-    // otherwise only the edge ring, since the interior was at a local fixed point
-    // when this CTA or an earlier one last stored the tile and only the halo changed.
-    static __device__ void seed_wave(const Smem &s, const EngineArgs &a, uint16_t *ovf, bool full) {
+    // Initial wave of a visit, into buffer 0; returns its size. A pixel enters it when one
+    // Jacobi step of Eq. "recon" raises it: J(p) < min(I(p), max of J over N_G(p)).
+    // full: every owned pixel is tested (first visit); otherwise only the edge ring, since
+    // the interior was at a local fixed point when it was last stored and only the halo can
+    // have changed since.
+    static __device__ uint32_t seed_wave(const Smem &s, const EngineArgs &a, uint16_t *ovf, bool full,
+                                         unsigned long long &rows, int lane) {
         const int n = full ? NPIX : NRING;
-        const int nround = (n + kThreads - 1) / kThreads * kThreads;
-        for (int i = threadIdx.x; i < nround; i += kThreads) {
-            bool w[1] = {false};
+        const int nround = (n + 31) / 32 * 32;
+        uint32_t cnt = 0;
+        for (int i = lane; i < nround; i += 32) {
             int q[1] = {0};
+            uint32_t cm = 0;
             if (i < n) {
                 int r, c;
-                if (full) { r = i / TW + 1; c = i % TW + 1; }
+                if (full) { r = i / TW + 1; c = i % TW; }
                 else ring_rc(i, r, c);
-                const int p = r * PW + c;
-                if (seed_pixel(s, p)) {
-                    atomicOr(&s.inq[p >> 5], 1u << (p & 31));
-                    w[0] = true;
+                const int p = pidx(r, c);
+                uint32_t m = 0;
+#pragma unroll
+                for (int d = 0; d < NDIR; d++) m = max(m, val(s.J[p + nb_off(d)]));
+                const uint32_t nv = min(m, (uint32_t)s.I[p]);
+                if (nv > val(s.J[p])) {
+                    s.J[p] = (nv << 1) | QBIT;
+                    rows |= 1ull << (r - 1);
                     q[0] = p;
+                    cm = 1;
                 }
             }
-            push_warp<1>(s, a, ovf, 0, 0, w, q);
+            push_warp<1>(s, a, ovf, 0, cnt, cm, q, lane);
         }
+        __syncwarp();
+        return cnt;
     }
 
-    // Drain the wave queues to a local fixed point. Wave k reads buffer k&1 with count
-    // misc[M_QN + k%3], pushes into buffer (k+1)&1 / count (k+1)%3, and zeroes count
-    // (k+2)%3, whose readers all passed the barrier that opens wave k.
-    static __device__ uint32_t run_waves(const Smem &s, const EngineArgs &a, uint16_t *ovf,
-                                         uint32_t &seeds) {
+    static __device__ __forceinline__ int entry(const Smem &s, const EngineArgs &a, const uint16_t *ovf,
+                                                int buf, uint32_t i) {
+        return (i < a.qcap) ? s.q[buf * a.qcap + i] : ovf[buf * a.ovcap + (i - a.qcap)];
+    }
+
+    // Drain the wave queues to a local fixed point, starting from `n` entries in buffer 0.
+    static __device__ uint32_t run_waves(const Smem &s, const EngineArgs &a, uint16_t *ovf, uint32_t n,
+                                         unsigned long long &rows, uint32_t &waves, int lane) {
         uint32_t pops = 0;
-        seeds = 0;
+        waves = 0;
         volatile uint32_t *vJ = s.J;
-        for (int k = 0;; k++) {
-            const int cb = k & 1, nb = cb ^ 1;
-            const int cc = k % 3, nc = (k + 1) % 3, zc = (k + 2) % 3;
-            __syncthreads();
-            uint32_t n = s.misc[M_QN + cc];
-            if (n == 0) break;
-            if (n > a.qcap + a.ovcap) n = a.qcap + a.ovcap;   // cannot happen: entries are distinct pixels
-            if (threadIdx.x == 0) s.misc[M_QN + zc] = 0;
-            if (k == 0) seeds = n;
+        const uint32_t cap = a.qcap + a.ovcap;
+        int cb = 0;
+        while (n > 0) {
+            if (n > cap) n = cap;   // cannot happen: queued pixels are distinct
             pops += n;
-            const uint32_t nround = (n + kThreads - 1) / kThreads * kThreads;
-            for (uint32_t i = threadIdx.x; i < nround; i += kThreads) {
+            waves++;
+            const int nb = cb ^ 1;
+            uint32_t nn = 0;
+            const uint32_t nround = (n + 31) / 32 * 32;
+            for (uint32_t i = lane; i < nround; i += 32) {
                 const bool valid = i < n;
-                int p = 0;
-                if (valid) {
-                    p = (i < a.qcap) ? s.q[cb * a.qcap + i] : ovf[cb * a.ovcap + (i - a.qcap)];
-                    atomicAnd(&s.inq[p >> 5], ~(1u << (p & 31)));
-                }
-                __threadfence_block();
-                const uint32_t v = valid ? vJ[p] : 0u;
-                bool w[NDIR];
+                const int p = valid ? entry(s, a, ovf, cb, i) : pidx(1, 0);
+                const uint32_t v = valid ? val(atomicAnd(&s.J[p], ~QBIT)) : 0u;
                 int q[NDIR];
+                uint32_t nv[NDIR], cur[NDIR];
+#pragma unroll
+                for (int d = 0; d < NDIR; d++) {   // all neighbour reads first
+                    q[d] = p + nb_off(d);
+                    nv[d] = min(v, (uint32_t)s.I[q[d]]);
+                    cur[d] = val(vJ[q[d]]);
+                }
+                uint32_t cm = 0;
 #pragma unroll
                 for (int d = 0; d < NDIR; d++) {
-                    w[d] = false;
-                    q[d] = p + nb_off(d);
-                    if (valid) {
-                        const uint32_t nv = min(v, s.I[q[d]]);
-                        if (vJ[q[d]] < nv) {
-                            const uint32_t old = atomicMax(&s.J[q[d]], nv);
-                            if (old < nv) {
-                                s.rowchg[q[d] / PW - 1] = 1;
-                                __threadfence_block();
-                                const uint32_t bit = 1u << (q[d] & 31);
-                                w[d] = (atomicOr(&s.inq[q[d] >> 5], bit) & bit) == 0;
-                            }
+                    if (cur[d] < nv[d]) {
+                        const uint32_t wnew = (nv[d] << 1) | QBIT;
+                        const uint32_t old = atomicMax(&s.J[q[d]], wnew);
+                        if (old < wnew) {
+                            if (val(old) < nv[d]) mark_row(rows, q[d]);
+                            if ((old & QBIT) == 0) cm |= 1u << d;
                         }
                     }
                 }
-                push_warp<NDIR>(s, a, ovf, nb, nc, w, q);
+                push_warp<NDIR>(s, a, ovf, nb, nn, cm, q, lane);
             }
+            __syncwarp();
+            n = nn;
+            cb = nb;
         }
         return pops;
     }
 
     // ---- end of a visit -----------------------------------------------------------------------
-    // For every edge pixel raised in this visit, test its halo neighbours with the
-    // propagation condition J(q) < min(J(p), I(q)); flag the neighbour tiles to notify.
-    static __device__ void notify_scan(const Smem &s) {
-        for (int i = threadIdx.x; i < NRING; i += kThreads) {
+    // For every halo pixel h: can the tile's pixels raise it above the value it had when it
+    // was loaded (one Jacobi step from the tile's own pixels, or a raise already made)? If so
+    // the neighbour tile that owns h has work: flag it.
+    static __device__ void notify_scan(const Smem &s, int lane) {
+        for (int i = lane; i < NHALO; i += 32) {
             int r, c;
-            ring_rc(i, r, c);
-            const int p = r * PW + c;
-            const uint32_t v = s.J[p];
-            if (v == s.ring0[i]) continue;
+            halo_rc(i, r, c);
+            const int h = pidx(r, c);
+            uint32_t m = 0;
 #pragma unroll
             for (int d = 0; d < NDIR; d++) {
                 const int qr = r + dir_dy(d), qc = c + dir_dx(d);
-                if (!is_halo(qr, qc)) continue;
-                const uint32_t hq = s.J[qr * PW + qc];
-                if (hq < min(v, s.haloI[halo_index(qr, qc)])) {
-                    const int dy = qr == 0 ? -1 : (qr == PH - 1 ? 1 : 0);
-                    const int dx = qc == 0 ? -1 : (qc == PW - 1 ? 1 : 0);
-                    s.misc[M_NOTIFY + (dy + 1) * 3 + (dx + 1)] = 1;
-                }
+                if (qr >= 1 && qr <= TH && qc >= 0 && qc < TW) m = max(m, val(s.J[h + nb_off(d)]));
+            }
+            const uint32_t nv = max(val(s.J[h]), min(m, (uint32_t)s.I[h]));
+            if (nv > s.halo0[i]) {
+                const int dy = r == 0 ? -1 : (r == PH - 1 ? 1 : 0);
+                const int dx = c < 0 ? -1 : (c >= TW ? 1 : 0);
+                s.misc[M_NOTIFY + (dy + 1) * 3 + (dx + 1)] = 1;
             }
         }
     }
 
-    static __device__ void save_ring(const Smem &s) {
-        for (int i = threadIdx.x; i < NRING; i += kThreads) {
-            int r, c;
-            ring_rc(i, r, c);
-            s.ring0[i] = s.J[r * PW + c];
+    // Whole warp, after a fence and __syncwarp: lane j notifies neighbour j.
+    static __device__ void send_notifications(const Smem &s, const EngineArgs &a, int ty, int tx, int lane) {
+        if (lane < 9 && lane != 4 && s.misc[M_NOTIFY + lane]) {
+            const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+            if (ny >= 0 && nx >= 0 && ny < a.img.tiles_y && nx < a.img.tiles_x)
+                notify_tile(a, (uint32_t)(ny * a.img.tiles_x + nx));
         }
     }
 
-    // Called by thread 0 after a fence and a barrier: notify flagged neighbours.
-    static __device__ void send_notifications(const Smem &s, const EngineArgs &a, int ty, int tx) {
-        for (int j = 0; j < 9; j++) {
-            if (j == 4 || !s.misc[M_NOTIFY + j]) continue;
-            const int ny = ty + j / 3 - 1, nx = tx + j % 3 - 1;
-            if (ny < 0 || nx < 0 || ny >= a.img.tiles_y || nx >= a.img.tiles_x) continue;
-            notify_tile(a, (uint32_t)(ny * a.img.tiles_x + nx));
-        }
-    }
-
-    static __device__ void clear_visit_flags(const Smem &s, bool clear_inq) {
-        for (int i = threadIdx.x; i < TH; i += kThreads) s.rowchg[i] = 0;
-        if (threadIdx.x < 9) s.misc[M_NOTIFY + threadIdx.x] = 0;
-        if (threadIdx.x < 3) s.misc[M_QN + threadIdx.x] = 0;
-        if (threadIdx.x == 0) { s.misc[M_FLAG] = 0; s.misc[M_PRECOND] = 0; }
-        if (clear_inq)
-            for (int i = threadIdx.x; i < INQ_WORDS; i += kThreads) s.inq[i] = 0;
+    static __device__ void clear_flags(const Smem &s, int lane) {
+        if (lane < 10) s.misc[lane] = 0;
+        __syncwarp();
     }
 };
 
 // ---- kernel 1: tile-parallel scan -------------------------------------------------------------
-// Per tile: precondition check, `sweeps` raster/anti-raster pairs in shared memory,
-// store, then frontier initialisation: queue the tile if one of its pixels can still be
-// raised, and its neighbours if a raised edge pixel can raise one of theirs.
+// Per tile (one warp each): precondition check, `sweeps` raster / anti-raster pairs in
+// shared memory, store, then frontier initialisation: queue the tile if one of its
+// pixels can still be raised, and each neighbour one of whose halo pixels it can raise.
 template <typename T, int CONN, int TH, int TW>
 __global__ void __launch_bounds__(kThreads) scan_kernel(EngineArgs a) {
     using TL = Tile<T, CONN, TH, TW>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    const typename TL::Smem s = TL::carve(smem_raw);
-    for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const typename TL::Smem s = TL::carve(smem_raw + warp * TL::smem_per_warp(a.qcap));
+    const uint32_t nworkers = gridDim.x * kWarpsPerCta;
+    for (uint32_t t = blockIdx.x * kWarpsPerCta + warp; t < a.ntiles; t += nworkers) {
         const int ty = t / a.img.tiles_x, tx = t % a.img.tiles_x;
-        TL::clear_visit_flags(s, false);
-        TL::zero_outside(a.img, s, ty, tx, true, true);
-        TL::load_rows(a.img, s, ty, tx, 0, TL::PH, true, true, false);
-        __syncthreads();
+        TL::clear_flags(s, lane);
+        TL::load_tile(a.img, s, ty, tx, lane);
+        TL::save_halo(s, lane);
         bool bad = false;
-        for (int i = threadIdx.x; i < TL::NPIX; i += kThreads) {
-            const int p = (i / TW + 1) * TL::PW + (i % TW + 1);
-            bad |= s.J[p] > s.I[p];
+        for (int i = lane; i < TL::NPIX; i += 32) {
+            const int p = TL::pidx(i / TW + 1, i % TW);
+            bad |= TL::val(s.J[p]) > (uint32_t)s.I[p];
         }
-        if (bad) s.misc[TL::M_PRECOND] = 1;
-        TL::save_ring(s);
-        __syncthreads();
+        bad = __any_sync(0xffffffffu, bad);
+        unsigned long long rows = 0;
         for (int k = 0; k < a.sweeps; k++) {
-            TL::sweep_raster(s);
-            __syncthreads();
-            TL::sweep_antiraster(s);
-            __syncthreads();
+            rows |= TL::sweep_raster(s, lane);
+            rows |= TL::sweep_antiraster(s, lane);
         }
-        if (a.sweeps > 0) TL::store_rows(a.img, s, ty, tx, false);
+        if (rows) TL::store_tile(a.img, s, ty, tx, rows, false, lane);
         bool active = false;
-        for (int i = threadIdx.x; i < TL::NPIX; i += kThreads) {
-            const int p = (i / TW + 1) * TL::PW + (i % TW + 1);
+        for (int i = lane; i < TL::NPIX; i += 32) {
+            const int p = TL::pidx(i / TW + 1, i % TW);
             uint32_t m = 0;
 #pragma unroll
-            for (int d = 0; d < TL::NDIR; d++) m = max(m, s.J[p + TL::nb_off(d)]);
-            active |= min(m, s.I[p]) > s.J[p];
+            for (int d = 0; d < TL::NDIR; d++) m = max(m, TL::val(s.J[p + TL::nb_off(d)]));
+            active |= min(m, (uint32_t)s.I[p]) > TL::val(s.J[p]);
         }
-        if (active) s.misc[TL::M_FLAG] = 1;
-        TL::notify_scan(s);
+        active = __any_sync(0xffffffffu, active);
+        TL::notify_scan(s, lane);
         __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (s.misc[TL::M_PRECOND]) set_status(a.hdr, kErrPrecondition);
-            if (s.misc[TL::M_FLAG]) notify_tile(a, t);
-            TL::send_notifications(s, a, ty, tx);
+        __syncwarp();
+        if (lane == 0) {
+            if (bad) set_status(a.hdr, kErrPrecondition);
+            if (active) notify_tile(a, t);
         }
-        __syncthreads();
+        TL::send_notifications(s, a, ty, tx, lane);
+        __syncwarp();
     }
 }
 
-// ---- kernel 2: persistent drain -------------------------------------------------------------
+// ---- kernel 2: persistent drain (every warp is a worker) ----------------------------------------
 template <typename T, int CONN, int TH, int TW>
-__global__ void __launch_bounds__(kThreads) drain_kernel(EngineArgs a) {
+__global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_kernel(EngineArgs a) {
     using TL = Tile<T, CONN, TH, TW>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    const typename TL::Smem s = TL::carve(smem_raw);
-    uint16_t *ovf = a.ovf + (size_t)blockIdx.x * 2 * a.ovcap;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const typename TL::Smem s = TL::carve(smem_raw + warp * TL::smem_per_warp(a.qcap));
+    uint16_t *ovf = a.ovf + ((size_t)blockIdx.x * kWarpsPerCta + warp) * 2 * a.ovcap;
+    unsigned long long visits = 0, pops_total = 0, seeds_total = 0, waves_total = 0;
+    unsigned long long idle = 0, busy = 0, tmark = 0;
+#if IWPP_PHASE_TIMING
+    unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#endif
     for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t t = pop_tile(a);
-            s.misc[TL::M_TILE] = t;
+        uint32_t t = 0, first = 0;
+        if (lane == 0) {
+            tmark = globaltimer_ns();
+            t = pop_tile(a);
+            const unsigned long long now = globaltimer_ns();
+            idle += now - tmark;
+            tmark = now;
             if (t != kDone) {
                 const uint32_t old = atomicAdd(a.state + t, 1u);   // PENDING -> ACTIVE
-                const bool first = (old & ST_VISITED) == 0;
+                first = (old & ST_VISITED) == 0;
                 if (first) atomicOr(a.state + t, ST_VISITED);
-                s.misc[TL::M_FIRST] = first;
                 __threadfence();
             }
         }
-        __syncthreads();
-        const uint32_t t = s.misc[TL::M_TILE];
+        t = __shfl_sync(0xffffffffu, t, 0);
+        first = __shfl_sync(0xffffffffu, first, 0);
         if (t == kDone) break;
-        const bool first = s.misc[TL::M_FIRST] != 0;
         const int ty = t / a.img.tiles_x, tx = t % a.img.tiles_x;
-        TL::clear_visit_flags(s, true);
-        TL::zero_outside(a.img, s, ty, tx, true, true);
-        TL::load_rows(a.img, s, ty, tx, 0, TL::PH, true, true, true);
-        __syncthreads();
-        bool full = first;
+#if IWPP_PHASE_TIMING
+        long long c0 = clock64();
+#define IWPP_PHASE(k) do { const long long c1 = clock64(); if (lane == 0) ph[k] += c1 - c0; c0 = c1; } while (0)
+#else
+#define IWPP_PHASE(k) do { } while (0)
+#endif
+        TL::clear_flags(s, lane);
+        TL::load_tile(a.img, s, ty, tx, lane);
+        TL::save_halo(s, lane);
+        IWPP_PHASE(0);
+        bool full = first != 0;
         for (;;) {
-            TL::save_ring(s);
-            __syncthreads();
+            unsigned long long rows = 0;
             if (full) {
                 for (int k = 0; k < a.revisit_sweeps; k++) {
-                    TL::sweep_raster(s);
-                    __syncthreads();
-                    TL::sweep_antiraster(s);
-                    __syncthreads();
+                    rows |= TL::sweep_raster(s, lane);
+                    rows |= TL::sweep_antiraster(s, lane);
                 }
             }
-            TL::seed_wave(s, a, ovf, full);
-            uint32_t seeds;
-            const uint32_t pops = TL::run_waves(s, a, ovf, seeds);
-            TL::store_rows(a.img, s, ty, tx, true);
-            TL::notify_scan(s);
+            const uint32_t seeds = TL::seed_wave(s, a, ovf, full, rows, lane);
+            IWPP_PHASE(1);
+            uint32_t waves;
+            const uint32_t pops = TL::run_waves(s, a, ovf, seeds, rows, waves, lane);
+            IWPP_PHASE(2);
+            visits++;
+            pops_total += pops;
+            seeds_total += seeds;
+            waves_total += waves;
+            rows = (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)rows) |
+                   ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(rows >> 32)) << 32);
+            if (rows) TL::store_tile(a.img, s, ty, tx, rows, true, lane);
+            TL::notify_scan(s, lane);
+            IWPP_PHASE(3);
             __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                TL::send_notifications(s, a, ty, tx);
-                atomicAdd(&a.hdr->visits, 1ull);
-                atomicAdd(&a.hdr->pops, (unsigned long long)pops);
-                atomicAdd(&a.hdr->seeds, (unsigned long long)seeds);
-                const uint32_t busy = ST_ACTIVE | ST_VISITED;
-                const uint32_t r = atomicCAS(a.state + t, busy, ST_VISITED);
-                uint32_t redo = 0;
-                if (r == busy) {
+            __syncwarp();
+            IWPP_PHASE(4);
+            TL::send_notifications(s, a, ty, tx, lane);
+            IWPP_PHASE(5);
+            uint32_t redo = 0;
+            if (lane == 0) {
+                const uint32_t busy_st = ST_ACTIVE | ST_VISITED;
+                const uint32_t r = atomicCAS(a.state + t, busy_st, ST_VISITED);
+                if (r == busy_st) {
                     __threadfence();
                     atomicSub(&a.hdr->pending, 1u);
                 } else {
@@ -744,17 +812,34 @@ __global__ void __launch_bounds__(kThreads) drain_kernel(EngineArgs a) {
                     redo = 1;
                 }
                 __threadfence();
-                s.misc[TL::M_REDO] = redo && !fatal(a.hdr);   // one decision for the whole CTA
+                redo = redo && !fatal(a.hdr);
             }
-            __syncthreads();
-            if (!s.misc[TL::M_REDO]) break;
-            // Re-process: the interior in shared memory is what this CTA stored; only the
+            redo = __shfl_sync(0xffffffffu, redo, 0);
+            IWPP_PHASE(6);
+            if (!redo) {
+                if (lane == 0) busy += globaltimer_ns() - tmark;
+                break;
+            }
+            // Re-process: the interior in shared memory is what this warp stored; only the
             // halo can have changed since.
-            TL::clear_visit_flags(s, false);
-            TL::load_halo_J(a.img, s, ty, tx);
+            TL::clear_flags(s, lane);
+            TL::load_halo_J(a.img, s, ty, tx, lane);
+            TL::save_halo(s, lane);
             full = false;
-            __syncthreads();
+            IWPP_PHASE(7);
         }
+#undef IWPP_PHASE
+    }
+    if (lane == 0) {
+        atomicAdd(&a.hdr->visits, visits);
+        atomicAdd(&a.hdr->pops, pops_total);
+        atomicAdd(&a.hdr->seeds, seeds_total);
+        atomicAdd(&a.hdr->waves, waves_total);
+        atomicAdd(&a.hdr->idle_ns, idle);
+        atomicAdd(&a.hdr->busy_ns, busy);
+#if IWPP_PHASE_TIMING
+        for (int k = 0; k < 8; k++) atomicAdd(&a.hdr->phase_cycles[k], ph[k]);
+#endif
     }
 }
 

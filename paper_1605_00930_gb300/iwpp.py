@@ -130,11 +130,12 @@ def iwpp_sync_status(ws_ptr, stream) -> int:
 
 
 def iwpp_work_counters(ws_ptr, stream):
-    out = (ctypes.c_uint64 * 3)()
+    out = (ctypes.c_uint64 * 6)()
     rc = lib().iwpp_work_counters(ws_ptr, stream, out)
     if rc != 0:
         raise IwppError(rc, "iwpp_work_counters")
-    return {"visits": int(out[0]), "pops": int(out[1]), "seeds": int(out[2])}
+    return {"visits": int(out[0]), "pops": int(out[1]), "seeds": int(out[2]), "waves": int(out[3]),
+            "idle_ns": int(out[4]), "busy_ns": int(out[5])}
 
 
 # ---- torch convenience layer -----------------------------------------------------------

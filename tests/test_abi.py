@@ -46,9 +46,10 @@ def test_library_exports_every_declared_symbol(iwpp):
 
 def test_default_plan_and_shapes(iwpp):
     p = iwpp.iwpp_default_plan()
-    assert (p.tile_h, p.tile_w) == (64, 64)
+    assert iwpp.iwpp_tile_shape_supported(p.tile_h, p.tile_w)
     assert p.sweeps >= 0 and 16 <= p.smem_queue_cap <= p.tile_h * p.tile_w
-    assert iwpp.iwpp_tile_shape_supported(64, 64)
+    for shape in [(32, 32), (32, 64), (64, 64)]:
+        assert iwpp.iwpp_tile_shape_supported(*shape)
     assert not iwpp.iwpp_tile_shape_supported(48, 48)
 
 

@@ -70,7 +70,7 @@ def _random_pair(rng, H, W, dtype, op, vmax):
     return marker, mask
 
 
-SHAPES = [(1, 1), (1, 700), (700, 1), (64, 64), (65, 130), (129, 65), (200, 333), (257, 513)]
+SHAPES = [(1, 1), (1, 700), (700, 1), (32, 32), (64, 64), (65, 130), (129, 65), (200, 333), (257, 513)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -91,7 +91,7 @@ def test_hand_cases_gpu(iw, case):
         np.testing.assert_array_equal(got, case["expected"])
 
 
-@pytest.mark.parametrize("tile", [(64, 64), (32, 64), (64, 128)])
+@pytest.mark.parametrize("tile", [(32, 32), (32, 64), (64, 64)])
 @pytest.mark.parametrize("sweeps", [0, 1, 3])
 @pytest.mark.parametrize("qcap", [16, 1024])
 def test_plans_tissue(iw, oracle_lib, tile, sweeps, qcap):

@@ -146,7 +146,61 @@ IWPP_API int iwpp_drain(void *marker_inout, const void *mask, int64_t H, int64_t
 IWPP_API int iwpp_sync_status(const void *workspace, void *stream);
 
 /*
- * Work counters of the last single-image call that used `workspace`: tile
+ * ---- Batches (one persistent launch over many images) -------------------------
+ * One image of a batch. Images may differ in size, pixel type, operator and
+ * connectivity; the same conventions as for a single image apply to each.
+ * reserved must be 0.
+ */
+typedef struct {
+    void *marker_inout;
+    const void *mask;
+    int64_t H, W;
+    int32_t connectivity, op, dtype, reserved;
+} iwpp_image;
+
+/* Number of tiles of a batch under `plan` (NULL = default plan), or -1 for a bad
+ * argument. Tiles are numbered image by image (in the order of `imgs`),
+ * row-major inside an image; this numbering indexes the per-tile arrays of
+ * iwpp_reconstruct_batch_sched. Host-only call. */
+IWPP_API int64_t iwpp_batch_tile_count(const iwpp_image *imgs, int n, const iwpp_plan *plan);
+
+/* Workspace bytes needed by iwpp_reconstruct_batch(_sched) for this batch on the
+ * current device (0 for a bad argument). */
+IWPP_API size_t iwpp_batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan);
+
+/*
+ * Reconstruction of every image of a batch (each result identical to a separate
+ * iwpp_reconstruct call) in one persistent launch: the image table is written
+ * into the workspace by small kernels that take the descriptors as parameters,
+ * a scan kernel runs over every tile of every image (precondition check,
+ * tile-local sweeps, frontier initialisation), a compact kernel queues the tiles
+ * that can still change in schedule order, and one persistent kernel drains the
+ * whole batch. `imgs` is a HOST array of n >= 1 descriptors, read during the call
+ * only. No host synchronisation and no allocation: the call can be captured in a
+ * CUDA graph (the descriptors are then frozen into the graph).
+ */
+IWPP_API int iwpp_reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan, void *workspace,
+                                    size_t ws_bytes, void *stream);
+
+/*
+ * As iwpp_reconstruct_batch, with an explicit schedule in DEVICE memory (each
+ * pointer may be NULL):
+ *   tile_order   uint32[ntiles]: the order in which the initial frontier is
+ *                queued (a permutation of the tile ids; repeated or missing ids
+ *                are tolerated: a tile is queued once, missing ones at the end)
+ *   tile_sweeps  uint8[ntiles]: raster / anti-raster sweep pairs of each tile in
+ *                the scan kernel (else plan->sweeps for every tile)
+ *   tile_work    uint32[2 * ntiles], caller-zeroed: receives per-tile work, [t] =
+ *                wave-queue pops, [ntiles + t] = SM cycles spent on the tile
+ * The schedule changes the work done, never the result.
+ */
+IWPP_API int iwpp_reconstruct_batch_sched(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                          const uint32_t *tile_order, const uint8_t *tile_sweeps,
+                                          uint32_t *tile_work, void *workspace, size_t ws_bytes,
+                                          void *stream);
+
+/*
+ * Work counters of the last call (single image or batch) that used `workspace`: tile
  * visits by the persistent kernel, wave-queue entries processed (pops),
  * entries created by the visits' initial scans (seeds), wave steps run, and
  * the persistent workers' summed waiting time and processing time in ns.

@@ -1,23 +1,31 @@
-// iwpp_api.cu — C ABI of the single-image reconstruction path (include/iwpp.h).
+// iwpp_api.cu — C ABI of the reconstruction paths (include/iwpp.h).
 //
-// Host side only validates arguments, carves the caller's workspace and enqueues
-// three steps on the caller's stream: a workspace reset (memsets), the
-// tile-parallel scan kernel (precondition check, tile-local raster / anti-raster
-// sweeps of Algorithm 7, frontier initialisation), and the persistent drain
-// kernel (Algorithm 7's irregular propagation phase). No host synchronisation,
-// no allocation.
+// Host code only validates arguments, carves the caller's workspace and enqueues
+// kernels on the caller's stream:
+//   single image: workspace reset (memsets) -> tile-parallel scan kernel
+//     (precondition check, tile-local raster / anti-raster sweeps of Algorithm 7,
+//     frontier initialisation) -> persistent drain kernel (Algorithm 7's irregular
+//     propagation phase);
+//   batch: image-table upload (descriptors as kernel parameters) -> reset -> mixed
+//     scan kernel over every tile of every image (per-tile sweep counts) -> compact
+//     kernel (initial frontier queued in schedule order) -> one persistent drain
+//     over the whole batch.
+// No host synchronisation and no allocation on these paths, so they can be captured
+// in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/iwpp.h"
 #include "iwpp_engine.cuh"
+#include "iwpp_host.h"
 
 namespace iwpp {
 
-// ---- compiled tile shapes -------------------------------------------------------------------
+// ---- compiled tile shapes ---------------------------------------------------------------------
 struct ShapeInfo {
     int th, tw;
 };
@@ -30,13 +38,14 @@ int shape_index(int th, int tw) {
     return -1;
 }
 
-// Kernel table: [shape][dtype][conn4/8]
+// A scan / drain kernel pair with its shared-memory size function. Index [shape][v]:
+// v = 0..3 single-image kinds (bit 0 = u16, bit 1 = 8-connectivity), v = 4 mixed batch.
 struct KernelSet {
     void (*scan)(EngineArgs);
     void (*drain)(EngineArgs);
     size_t (*smem)(uint32_t);
-    int npix;
 };
+static constexpr int kMixed = 4;
 
 template <typename T, int CONN, int TH, int TW>
 static KernelSet make_set() {
@@ -44,20 +53,27 @@ static KernelSet make_set() {
     k.scan = scan_kernel<T, CONN, TH, TW>;
     k.drain = drain_kernel<T, CONN, TH, TW>;
     k.smem = &Tile<T, CONN, TH, TW>::smem_bytes;
-    k.npix = TH * TW;
     return k;
 }
 
 template <int TH, int TW>
-static void fill_shape(KernelSet (&row)[2][2]) {
-    row[0][0] = make_set<uint8_t, 4, TH, TW>();
-    row[0][1] = make_set<uint8_t, 8, TH, TW>();
-    row[1][0] = make_set<uint16_t, 4, TH, TW>();
-    row[1][1] = make_set<uint16_t, 8, TH, TW>();
+static size_t mixed_smem_bytes(uint32_t qcap) {
+    return mixed_smem_per_warp<TH, TW>(qcap) * kWarpsPerCta;
 }
 
-static KernelSet g_sets[kNumShapes][2][2];
-static int g_maxsmem_set[kNumShapes][2][2];
+template <int TH, int TW>
+static void fill_shape(KernelSet (&row)[5]) {
+    row[0] = make_set<uint8_t, 4, TH, TW>();
+    row[1] = make_set<uint16_t, 4, TH, TW>();
+    row[2] = make_set<uint8_t, 8, TH, TW>();
+    row[3] = make_set<uint16_t, 8, TH, TW>();
+    row[kMixed].scan = scan_mixed_kernel<TH, TW>;
+    row[kMixed].drain = drain_mixed_kernel<TH, TW>;
+    row[kMixed].smem = &mixed_smem_bytes<TH, TW>;
+}
+
+static KernelSet g_sets[kNumShapes][5];
+static int g_smem_set[kNumShapes][5];
 static std::once_flag g_once;
 static std::mutex g_mu;
 
@@ -67,18 +83,20 @@ static void init_sets() {
     fill_shape<64, 64>(g_sets[2]);
 }
 
-const KernelSet &kernels(int shape, int dtype, int conn) {
+static int kind_of(int dtype, int conn) { return (dtype == IWPP_U16 ? 1 : 0) | (conn == 8 ? 2 : 0); }
+
+const KernelSet &kernels(int shape, int v) {
     std::call_once(g_once, init_sets);
-    return g_sets[shape][dtype][conn == 8 ? 1 : 0];
+    return g_sets[shape][v];
 }
 
-// Opt the kernels of one set into the dynamic shared memory they need (per device
-// the attribute is per function; set it once with a generous bound).
-static cudaError_t ensure_smem_attr(int shape, int dtype, int conn, size_t bytes) {
+// Opt a kernel pair into the dynamic shared memory it needs (set once per process with
+// a generous bound; the attribute belongs to the function).
+static cudaError_t ensure_smem_attr(int shape, int v, size_t bytes) {
     std::lock_guard<std::mutex> lk(g_mu);
-    int &done = g_maxsmem_set[shape][dtype][conn == 8 ? 1 : 0];
+    int &done = g_smem_set[shape][v];
     if ((size_t)done >= bytes) return cudaSuccess;
-    const KernelSet &k = kernels(shape, dtype, conn);
+    const KernelSet &k = kernels(shape, v);
     const int want = (int)(bytes < 100 * 1024 ? 100 * 1024 : bytes);
     cudaError_t e = cudaFuncSetAttribute((const void *)k.scan, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     if (e != cudaSuccess) return e;
@@ -88,7 +106,7 @@ static cudaError_t ensure_smem_attr(int shape, int dtype, int conn, size_t bytes
     return cudaSuccess;
 }
 
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int device_sm_count() {
     int dev = 0, n = 0;
@@ -97,17 +115,18 @@ int device_sm_count() {
     return n;
 }
 
-// Persistent CTAs for a plan: blocks_per_sm (or the occupancy maximum) x SMs,
-// never more CTAs than needed to give every tile its own warp.
-int drain_grid(const iwpp_plan &p, int dtype, int conn, uint32_t ntiles) {
+// Persistent CTAs for a plan: blocks_per_sm (or the occupancy maximum) x SMs, never more
+// CTAs than needed to give every tile its own warp.
+static int drain_grid(const iwpp_plan &p, int v, uint32_t ntiles) {
     const int shape = shape_index(p.tile_h, p.tile_w);
-    const KernelSet &k = kernels(shape, dtype, conn);
+    const KernelSet &k = kernels(shape, v);
     const size_t smem = k.smem((uint32_t)p.smem_queue_cap);
-    if (ensure_smem_attr(shape, dtype, conn, smem) != cudaSuccess) return 0;
+    if (ensure_smem_attr(shape, v, smem) != cudaSuccess) return 0;
     int bps = p.blocks_per_sm;
     if (bps <= 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k.drain, kThreads, smem) != cudaSuccess)
             return 0;
+        if (bps <= 0) return 0;
     }
     const int sms = device_sm_count();
     long long g = (long long)bps * sms;
@@ -136,28 +155,63 @@ void default_plan(iwpp_plan *p) {
     p->watchdog_ns = 0;
 }
 
-// Workspace layout of a single-image call.
-struct Layout {
-    size_t hdr, state, queue, ovf, total;
-    uint32_t ntiles, ovcap;
-    int grid;
-};
-
 static bool image_ok(int64_t H, int64_t W) {
     return H >= 1 && W >= 1 && H < (1ll << 31) && W < (1ll << 31) &&
            (uint64_t)H * (uint64_t)W < (1ull << 32);
 }
 
-static bool make_layout(int64_t H, int64_t W, int dtype, int conn, const iwpp_plan &p, Layout &L) {
+static ImageView make_view(void *marker, const void *mask, int64_t H, int64_t W, int conn, int op, int dtype,
+                           const iwpp_plan &p, uint32_t tile_base) {
+    ImageView v;
+    v.J = static_cast<uint8_t *>(marker);
+    v.I = static_cast<const uint8_t *>(mask);
+    v.H = (int)H;
+    v.W = (int)W;
+    v.tiles_x = (int)((W + p.tile_w - 1) / p.tile_w);
+    v.tiles_y = (int)((H + p.tile_h - 1) / p.tile_h);
+    v.flip = op == IWPP_ERODE ? (dtype == IWPP_U8 ? 0xFFu : 0xFFFFu) : 0u;
+    v.tile_base = tile_base;
+    v.kind = (uint32_t)kind_of(dtype, conn);
+    v.pad = 0;
+    return v;
+}
+
+static void fill_common(EngineArgs &a, const iwpp_plan &p, uint8_t *base, size_t off_state, size_t off_queue,
+                        size_t off_ovf, uint32_t ntiles, uint32_t ovcap) {
+    a.hdr = reinterpret_cast<WsHeader *>(base);
+    a.state = reinterpret_cast<uint32_t *>(base + off_state);
+    a.queue = reinterpret_cast<uint32_t *>(base + off_queue);
+    a.ovf = reinterpret_cast<uint16_t *>(base + off_ovf);
+    a.ntiles = ntiles;
+    a.qcap = (uint32_t)p.smem_queue_cap;
+    a.ovcap = ovcap;
+    a.sweeps = p.sweeps;
+    a.revisit_sweeps = p.revisit_sweeps;
+    a.tile_sweeps = nullptr;
+    a.order = nullptr;
+    a.tile_work = nullptr;
+    a.defer_push = 0;
+    a.watchdog_ns = p.watchdog_ns > 0 ? p.watchdog_ns : 10ll * 1000 * 1000 * 1000;
+    a.imgs = nullptr;
+    a.nimg = 0;
+}
+
+// ---- single image ------------------------------------------------------------------------------
+// Workspace: header (256 B) | tile states | tile-queue slots | per-warp overflow queues.
+struct Layout {
+    size_t state, queue, ovf, total;
+    uint32_t ntiles, ovcap;
+    int grid;
+};
+
+static bool make_layout(int64_t H, int64_t W, int v, const iwpp_plan &p, Layout &L) {
     if (!image_ok(H, W)) return false;
     const uint64_t tx = (W + p.tile_w - 1) / p.tile_w, ty = (H + p.tile_h - 1) / p.tile_h;
     if (tx * ty >= (1ull << 31)) return false;
     L.ntiles = (uint32_t)(tx * ty);
-    L.grid = drain_grid(p, dtype, conn, L.ntiles);
+    L.grid = drain_grid(p, v, L.ntiles);
     if (L.grid <= 0) return false;
-    const uint32_t npix = (uint32_t)(p.tile_h * p.tile_w);
-    L.ovcap = npix - (uint32_t)p.smem_queue_cap;
-    L.hdr = 0;
+    L.ovcap = (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap);
     L.state = 256;
     L.queue = L.state + align256((size_t)L.ntiles * 4);
     L.ovf = L.queue + align256((size_t)L.ntiles * 4);
@@ -169,8 +223,7 @@ static bool make_layout(int64_t H, int64_t W, int dtype, int conn, const iwpp_pl
 enum { kPhaseScan = 1, kPhaseDrain = 2 };
 
 int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int conn, int op, int dtype,
-                    const iwpp_plan *plan_in, void *ws, size_t ws_bytes, cudaStream_t stream,
-                    int phases) {
+                    const iwpp_plan *plan_in, void *ws, size_t ws_bytes, cudaStream_t stream, int phases) {
     if (!marker || !mask) return IWPP_ERR_ARG;
     if (((uintptr_t)marker & 15) || ((uintptr_t)mask & 15)) return IWPP_ERR_ARG;
     if (!image_ok(H, W)) return IWPP_ERR_ARG;
@@ -181,37 +234,23 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
     if (plan_in) p = *plan_in; else default_plan(&p);
     if (!plan_valid(p)) return IWPP_ERR_ARG;
     if (!ws || ((uintptr_t)ws & 255)) return IWPP_ERR_WORKSPACE;
+    const int v = kind_of(dtype, conn);
     Layout L;
-    if (!make_layout(H, W, dtype, conn, p, L)) return IWPP_ERR_CUDA;
+    if (!make_layout(H, W, v, p, L)) return IWPP_ERR_CUDA;
     if (ws_bytes < L.total) return IWPP_ERR_WORKSPACE;
 
     uint8_t *base = static_cast<uint8_t *>(ws);
     EngineArgs a;
-    a.img.J = static_cast<uint8_t *>(marker);
-    a.img.I = static_cast<const uint8_t *>(mask);
-    a.img.H = (int)H;
-    a.img.W = (int)W;
-    a.img.tiles_x = (int)((W + p.tile_w - 1) / p.tile_w);
-    a.img.tiles_y = (int)((H + p.tile_h - 1) / p.tile_h);
-    a.img.flip = op == IWPP_ERODE ? (dtype == IWPP_U8 ? 0xFFu : 0xFFFFu) : 0u;
-    a.hdr = reinterpret_cast<WsHeader *>(base + L.hdr);
-    a.state = reinterpret_cast<uint32_t *>(base + L.state);
-    a.queue = reinterpret_cast<uint32_t *>(base + L.queue);
-    a.ovf = reinterpret_cast<uint16_t *>(base + L.ovf);
-    a.ntiles = L.ntiles;
-    a.qcap = (uint32_t)p.smem_queue_cap;
-    a.ovcap = L.ovcap;
-    a.sweeps = p.sweeps;
-    a.revisit_sweeps = p.revisit_sweeps;
-    a.watchdog_ns = p.watchdog_ns > 0 ? p.watchdog_ns : 10ll * 1000 * 1000 * 1000;
+    fill_common(a, p, base, L.state, L.queue, L.ovf, L.ntiles, L.ovcap);
+    a.img0 = make_view(marker, mask, H, W, conn, op, dtype, p, 0);
 
     const int shape = shape_index(p.tile_h, p.tile_w);
-    const KernelSet &k = kernels(shape, dtype, conn);
+    const KernelSet &k = kernels(shape, v);
     const size_t smem = k.smem(a.qcap);
-    if (ensure_smem_attr(shape, dtype, conn, smem) != cudaSuccess) return IWPP_ERR_CUDA;
+    if (ensure_smem_attr(shape, v, smem) != cudaSuccess) return IWPP_ERR_CUDA;
 
     if (phases & kPhaseScan) {
-        if (cudaMemsetAsync(base, 0, L.queue, stream) != cudaSuccess) return IWPP_ERR_CUDA;  // header + state
+        if (cudaMemsetAsync(base, 0, L.queue, stream) != cudaSuccess) return IWPP_ERR_CUDA;  // header + states
         if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4, stream) != cudaSuccess)
             return IWPP_ERR_CUDA;
         const int sms = device_sm_count();
@@ -227,12 +266,129 @@ size_t workspace_bytes(int64_t H, int64_t W, int dtype, const iwpp_plan *plan_in
     iwpp_plan p;
     if (plan_in) p = *plan_in; else default_plan(&p);
     if (!plan_valid(p) || (dtype != 0 && dtype != 1)) return 0;
-    Layout L;
-    // conn does not change the layout; use the 8-connected kernels for the occupancy query
-    if (!make_layout(H, W, dtype, 8, p, L)) return 0;
-    Layout L4;
-    if (!make_layout(H, W, dtype, 4, p, L4)) return 0;
-    return L.total > L4.total ? L.total : L4.total;
+    size_t best = 0;
+    for (int conn = 4; conn <= 8; conn += 4) {   // the layout is the larger of the two kernels'
+        Layout L;
+        if (!make_layout(H, W, kind_of(dtype, conn), p, L)) return 0;
+        if (L.total > best) best = L.total;
+    }
+    return best;
+}
+
+// ---- batch -------------------------------------------------------------------------------------
+// Workspace: header (256 B) | image table | tile states | tile-queue slots | overflow queues.
+// Tiles are numbered image by image, row-major inside an image.
+struct BatchLayout {
+    size_t table, state, queue, ovf, total;
+    uint32_t ntiles, ovcap;
+    int grid;
+};
+
+static int check_image(const iwpp_image &d) {
+    if (!d.marker_inout || !d.mask) return IWPP_ERR_ARG;
+    if (((uintptr_t)d.marker_inout & 15) || ((uintptr_t)d.mask & 15)) return IWPP_ERR_ARG;
+    if (!image_ok(d.H, d.W)) return IWPP_ERR_ARG;
+    if (d.connectivity != 4 && d.connectivity != 8) return IWPP_ERR_ARG;
+    if (d.op != IWPP_DILATE && d.op != IWPP_ERODE) return IWPP_ERR_ARG;
+    if (d.dtype != IWPP_U8 && d.dtype != IWPP_U16) return IWPP_ERR_ARG;
+    return IWPP_OK;
+}
+
+// Total tiles of a batch (or -1 on a bad argument); bases[i] = first tile of image i.
+int64_t batch_tiles(const iwpp_image *imgs, int n, const iwpp_plan &p, std::vector<uint32_t> *bases) {
+    if (!imgs || n < 1) return -1;
+    uint64_t total = 0;
+    if (bases) bases->resize(n);
+    for (int i = 0; i < n; i++) {
+        if (check_image(imgs[i]) != IWPP_OK) return -1;
+        if (bases) (*bases)[i] = (uint32_t)total;
+        total += (uint64_t)((imgs[i].W + p.tile_w - 1) / p.tile_w) * (uint64_t)((imgs[i].H + p.tile_h - 1) / p.tile_h);
+        if (total >= (1ull << 31)) return -1;
+    }
+    return (int64_t)total;
+}
+
+static bool make_batch_layout(const iwpp_image *imgs, int n, const iwpp_plan &p, BatchLayout &L,
+                              std::vector<uint32_t> *bases) {
+    const int64_t nt = batch_tiles(imgs, n, p, bases);
+    if (nt < 1) return false;
+    L.ntiles = (uint32_t)nt;
+    L.grid = drain_grid(p, kMixed, L.ntiles);
+    if (L.grid <= 0) return false;
+    L.ovcap = (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap);
+    L.table = 256;
+    L.state = L.table + align256((size_t)n * sizeof(ImageView));
+    L.queue = L.state + align256((size_t)L.ntiles * 4);
+    L.ovf = L.queue + align256((size_t)L.ntiles * 4);
+    L.total = L.ovf + align256((size_t)L.grid * kWarpsPerCta * 2 * L.ovcap * sizeof(uint16_t) + 16);
+    return true;
+}
+
+size_t batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan_in) {
+    iwpp_plan p;
+    if (plan_in) p = *plan_in; else default_plan(&p);
+    if (!plan_valid(p)) return 0;
+    BatchLayout L;
+    if (!make_batch_layout(imgs, n, p, L, nullptr)) return 0;
+    return L.total;
+}
+
+int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, const uint32_t *order,
+                      const uint8_t *tile_sweeps, uint32_t *tile_work, void *ws, size_t ws_bytes,
+                      cudaStream_t stream) {
+    iwpp_plan p;
+    if (plan_in) p = *plan_in; else default_plan(&p);
+    if (!plan_valid(p)) return IWPP_ERR_ARG;
+    if (!imgs || n < 1) return IWPP_ERR_ARG;
+    for (int i = 0; i < n; i++)
+        if (check_image(imgs[i]) != IWPP_OK) return IWPP_ERR_ARG;
+    if (!ws || ((uintptr_t)ws & 255)) return IWPP_ERR_WORKSPACE;
+    std::vector<uint32_t> bases;
+    BatchLayout L;
+    if (!make_batch_layout(imgs, n, p, L, &bases)) return IWPP_ERR_ARG;
+    if (ws_bytes < L.total) return IWPP_ERR_WORKSPACE;
+
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    EngineArgs a;
+    fill_common(a, p, base, L.state, L.queue, L.ovf, L.ntiles, L.ovcap);
+    ImageView *table = reinterpret_cast<ImageView *>(base + L.table);
+    a.imgs = table;
+    a.nimg = n;
+    a.img0 = make_view(imgs[0].marker_inout, imgs[0].mask, imgs[0].H, imgs[0].W, imgs[0].connectivity,
+                       imgs[0].op, imgs[0].dtype, p, 0);
+    a.tile_sweeps = tile_sweeps;
+    a.order = order;
+    a.tile_work = tile_work;
+    a.defer_push = 1;
+
+    const int shape = shape_index(p.tile_h, p.tile_w);
+    const KernelSet &k = kernels(shape, kMixed);
+    const size_t smem = k.smem(a.qcap);
+    if (ensure_smem_attr(shape, kMixed, smem) != cudaSuccess) return IWPP_ERR_CUDA;
+
+    // image table: descriptors travel as kernel parameters (no host-to-device copy)
+    for (int first = 0; first < n; first += kDescChunk) {
+        DescChunk c;
+        c.first = first;
+        c.count = n - first < kDescChunk ? n - first : kDescChunk;
+        for (int j = 0; j < c.count; j++) {
+            const iwpp_image &d = imgs[first + j];
+            c.v[j] = make_view(d.marker_inout, d.mask, d.H, d.W, d.connectivity, d.op, d.dtype, p, bases[first + j]);
+        }
+        upload_descs_kernel<<<1, kDescChunk, 0, stream>>>(table, c);
+    }
+    if (cudaMemsetAsync(base, 0, 256, stream) != cudaSuccess) return IWPP_ERR_CUDA;
+    if (cudaMemsetAsync(base + L.state, 0, (size_t)L.ntiles * 4, stream) != cudaSuccess) return IWPP_ERR_CUDA;
+    if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4, stream) != cudaSuccess) return IWPP_ERR_CUDA;
+    const int sms = device_sm_count();
+    const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
+    k.scan<<<scan_grid, kThreads, smem, stream>>>(a);
+    const uint32_t cgrid = (L.ntiles + 255) / 256 < (uint32_t)(sms * 8) ? (L.ntiles + 255) / 256 : (uint32_t)(sms * 8);
+    compact_kernel<<<cgrid, 256, 0, stream>>>(a);
+    finalize_queue_kernel<<<cgrid, 256, 0, stream>>>(a);
+    k.drain<<<L.grid, kThreads, smem, stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
 }
 
 }  // namespace iwpp
@@ -278,6 +434,31 @@ extern "C" int iwpp_drain(void *marker_inout, const void *mask, int64_t H, int64
                           void *stream) {
     return iwpp::reconstruct_one(marker_inout, mask, H, W, connectivity, op, dtype, plan, workspace,
                                  ws_bytes, static_cast<cudaStream_t>(stream), iwpp::kPhaseDrain);
+}
+
+extern "C" int64_t iwpp_batch_tile_count(const iwpp_image *imgs, int n, const iwpp_plan *plan) {
+    iwpp_plan p;
+    if (plan) p = *plan; else iwpp::default_plan(&p);
+    if (!iwpp::plan_valid(p)) return -1;
+    return iwpp::batch_tiles(imgs, n, p, nullptr);
+}
+
+extern "C" size_t iwpp_batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan) {
+    return iwpp::batch_workspace_bytes(imgs, n, plan);
+}
+
+extern "C" int iwpp_reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan, void *workspace,
+                                      size_t ws_bytes, void *stream) {
+    return iwpp::reconstruct_batch(imgs, n, plan, nullptr, nullptr, nullptr, workspace, ws_bytes,
+                                   static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int iwpp_reconstruct_batch_sched(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                            const uint32_t *tile_order, const uint8_t *tile_sweeps,
+                                            uint32_t *tile_work, void *workspace, size_t ws_bytes,
+                                            void *stream) {
+    return iwpp::reconstruct_batch(imgs, n, plan, tile_order, tile_sweeps, tile_work, workspace, ws_bytes,
+                                   static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int iwpp_sync_status(const void *workspace, void *stream) {

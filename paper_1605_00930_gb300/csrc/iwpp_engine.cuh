@@ -90,25 +90,35 @@ static_assert(sizeof(WsHeader) <= 256, "header too large");
 
 // One image as the kernels see it.
 struct ImageView {
-    uint8_t *J;        // marker / result, row-major, pitch W elements
-    const uint8_t *I;  // mask
+    uint8_t *J;          // marker / result, row-major, pitch W elements
+    const uint8_t *I;    // mask
     int H, W;
     int tiles_x, tiles_y;
-    uint32_t flip;     // 0 for dilation, MAXV for erosion (complement = XOR)
+    uint32_t flip;       // 0 for dilation, MAXV for erosion (complement = XOR)
+    uint32_t tile_base;  // global id of the image's first tile
+    uint32_t kind;       // bit 0: u16 pixels; bit 1: 8-connectivity
+    uint32_t pad;
 };
 
-// Everything the kernels of one call share.
+// Everything the kernels of one call share. A single-image call uses img0; a batch
+// call reads its images from the device table `imgs` (sorted by tile_base).
 struct EngineArgs {
-    ImageView img;
+    ImageView img0;
+    const ImageView *imgs;       // batch table (nullptr for a single image)
+    int nimg;
     WsHeader *hdr;
-    uint32_t *state;    // ntiles words
-    uint32_t *queue;    // ntiles slots
-    uint16_t *ovf;      // per-warp overflow queues, 2 * ovcap entries each
+    uint32_t *state;             // ntiles words
+    uint32_t *queue;             // ntiles slots
+    uint16_t *ovf;               // per-warp overflow queues, 2 * ovcap entries each
     uint32_t ntiles;
-    uint32_t qcap;      // shared wave-queue entries per buffer
-    uint32_t ovcap;     // global overflow entries per buffer per warp
-    int sweeps;         // sweep pairs in the scan kernel
-    int revisit_sweeps; // sweep pairs at a tile's first persistent visit
+    uint32_t qcap;               // shared wave-queue entries per buffer
+    uint32_t ovcap;              // global overflow entries per buffer per warp
+    int sweeps;                  // sweep pairs in the scan kernel (when tile_sweeps is null)
+    int revisit_sweeps;          // sweep pairs at a tile's first persistent visit
+    const uint8_t *tile_sweeps;  // optional per-tile sweep pairs for the scan kernel
+    const uint32_t *order;       // optional order in which the initial frontier is queued
+    uint32_t *tile_work;         // optional per-tile counters: [t] pops, [ntiles + t] SM cycles
+    int defer_push;              // scan kernel marks tiles PENDING; the compact kernel queues them
     long long watchdog_ns;
 };
 
@@ -667,11 +677,12 @@ struct Tile {
     }
 
     // Whole warp, after a fence and __syncwarp: lane j notifies neighbour j.
-    static __device__ void send_notifications(const Smem &s, const EngineArgs &a, int ty, int tx, int lane) {
+    static __device__ void send_notifications(const Smem &s, const EngineArgs &a, const ImageView &im,
+                                              int ty, int tx, int lane) {
         if (lane < 9 && lane != 4 && s.misc[M_NOTIFY + lane]) {
             const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
-            if (ny >= 0 && nx >= 0 && ny < a.img.tiles_y && nx < a.img.tiles_x)
-                notify_tile(a, (uint32_t)(ny * a.img.tiles_x + nx));
+            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
+                notify_tile(a, im.tile_base + (uint32_t)(ny * im.tiles_x + nx));
         }
     }
 
@@ -681,166 +692,325 @@ struct Tile {
     }
 };
 
-// ---- kernel 1: tile-parallel scan -------------------------------------------------------------
-// Per tile (one warp each): precondition check, `sweeps` raster / anti-raster pairs in
-// shared memory, store, then frontier initialisation: queue the tile if one of its
-// pixels can still be raised, and each neighbour one of whose halo pixels it can raise.
+// ---- per-tile bodies shared by the single-image and the batch kernels -------------------------
+
+// Mark tile t PENDING without queueing it (the compact kernel queues it later, in order).
+__device__ inline void mark_pending(const EngineArgs &a, uint32_t t) {
+    const uint32_t old = atomicOr(a.state + t, ST_PENDING);
+    if ((old & (ST_PENDING | ST_ACTIVE)) == 0) atomicAdd(&a.hdr->pending, 1u);
+}
+
+// Tile-parallel scan of one tile (the frontier-initialisation kernel's body):
+// precondition check, `sweeps` raster / anti-raster pairs in shared memory, store, then
+// queue the tile if one of its pixels can still be raised, and each neighbour one of
+// whose halo pixels it can raise.
+template <typename T, int CONN, int TH, int TW>
+__device__ void scan_tile(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem, int lane) {
+    using TL = Tile<T, CONN, TH, TW>;
+    const typename TL::Smem s = TL::carve(wsmem);
+    const long long c0 = clock64();
+    const uint32_t lt = t - im.tile_base;
+    const int ty = lt / im.tiles_x, tx = lt % im.tiles_x;
+    TL::clear_flags(s, lane);
+    TL::load_tile(im, s, ty, tx, lane);
+    TL::save_halo(s, lane);
+    bool bad = false;
+    for (int i = lane; i < TL::NPIX; i += 32) {
+        const int p = TL::pidx(i / TW + 1, i % TW);
+        bad |= TL::val(s.J[p]) > (uint32_t)s.I[p];
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    const int sweeps = a.tile_sweeps ? (int)a.tile_sweeps[t] : a.sweeps;
+    unsigned long long rows = 0;
+    for (int k = 0; k < sweeps; k++) {
+        rows |= TL::sweep_raster(s, lane);
+        rows |= TL::sweep_antiraster(s, lane);
+    }
+    if (rows) TL::store_tile(im, s, ty, tx, rows, false, lane);
+    bool active = false;
+    for (int i = lane; i < TL::NPIX; i += 32) {
+        const int p = TL::pidx(i / TW + 1, i % TW);
+        uint32_t m = 0;
+#pragma unroll
+        for (int d = 0; d < TL::NDIR; d++) m = max(m, TL::val(s.J[p + TL::nb_off(d)]));
+        active |= min(m, (uint32_t)s.I[p]) > TL::val(s.J[p]);
+    }
+    active = __any_sync(0xffffffffu, active);
+    TL::notify_scan(s, lane);
+    __threadfence();
+    __syncwarp();
+    if (a.defer_push) {
+        if (lane < 9 && lane != 4 && s.misc[TL::M_NOTIFY + lane]) {
+            const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
+                mark_pending(a, im.tile_base + (uint32_t)(ny * im.tiles_x + nx));
+        }
+        if (lane == 0 && active) mark_pending(a, t);
+    } else {
+        if (lane == 0 && active) notify_tile(a, t);
+        TL::send_notifications(s, a, im, ty, tx, lane);
+    }
+    if (lane == 0) {
+        if (bad) set_status(a.hdr, kErrPrecondition);
+        if (a.tile_work) atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
+    }
+    __syncwarp();
+}
+
+struct VisitStats {
+    unsigned long long visits, pops, seeds, waves;
+};
+
+// One visit of tile t by the persistent kernel, including the re-processing rounds when
+// the tile is notified while this warp holds it. Lane 0 has already moved the tile to
+// ACTIVE; on return it is IDLE (or the run is stopping on an error).
+template <typename T, int CONN, int TH, int TW>
+__device__ void visit_tile(const EngineArgs &a, const ImageView &im, uint32_t t, bool first, uint8_t *wsmem,
+                           uint16_t *ovf, VisitStats &st, int lane) {
+    using TL = Tile<T, CONN, TH, TW>;
+    const typename TL::Smem s = TL::carve(wsmem);
+    const long long c0 = clock64();
+    const uint32_t lt = t - im.tile_base;
+    const int ty = lt / im.tiles_x, tx = lt % im.tiles_x;
+    TL::clear_flags(s, lane);
+    TL::load_tile(im, s, ty, tx, lane);
+    TL::save_halo(s, lane);
+    bool full = first;
+    uint32_t tile_pops = 0;
+    for (;;) {
+        unsigned long long rows = 0;
+        if (full) {
+            for (int k = 0; k < a.revisit_sweeps; k++) {
+                rows |= TL::sweep_raster(s, lane);
+                rows |= TL::sweep_antiraster(s, lane);
+            }
+        }
+        const uint32_t seeds = TL::seed_wave(s, a, ovf, full, rows, lane);
+        uint32_t waves;
+        const uint32_t pops = TL::run_waves(s, a, ovf, seeds, rows, waves, lane);
+        st.visits++;
+        st.pops += pops;
+        st.seeds += seeds;
+        st.waves += waves;
+        tile_pops += pops;
+        rows = (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)rows) |
+               ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(rows >> 32)) << 32);
+        if (rows) TL::store_tile(im, s, ty, tx, rows, true, lane);
+        TL::notify_scan(s, lane);
+        __threadfence();
+        __syncwarp();
+        TL::send_notifications(s, a, im, ty, tx, lane);
+        uint32_t redo = 0;
+        if (lane == 0) {
+            const uint32_t busy_st = ST_ACTIVE | ST_VISITED;
+            const uint32_t r = atomicCAS(a.state + t, busy_st, ST_VISITED);
+            if (r == busy_st) {
+                __threadfence();
+                atomicSub(&a.hdr->pending, 1u);
+            } else {
+                atomicAnd(a.state + t, ~ST_PENDING);   // notified while ACTIVE: go again
+                redo = 1;
+            }
+            __threadfence();
+            redo = redo && !fatal(a.hdr);
+        }
+        redo = __shfl_sync(0xffffffffu, redo, 0);
+        if (!redo) break;
+        // Re-process: the interior in shared memory is what this warp stored; only the
+        // halo can have changed since.
+        TL::clear_flags(s, lane);
+        TL::load_halo_J(im, s, ty, tx, lane);
+        TL::save_halo(s, lane);
+        full = false;
+    }
+    if (lane == 0 && a.tile_work) {
+        atomicAdd(a.tile_work + t, tile_pops);
+        atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
+    }
+}
+
+// Image that owns global tile t (binary search over tile_base in a batch).
+__device__ __forceinline__ const ImageView &image_of(const EngineArgs &a, uint32_t t) {
+    if (a.imgs == nullptr) return a.img0;
+    int lo = 0, hi = a.nimg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.imgs[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+    }
+    return a.imgs[lo];
+}
+
+// Pop the next tile (lane 0) and move it to ACTIVE; returns kDone when the run is over.
+__device__ inline uint32_t acquire_tile(const EngineArgs &a, bool &first, unsigned long long &idle, int lane) {
+    uint32_t t = 0, f = 0;
+    if (lane == 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        t = pop_tile(a);
+        idle += globaltimer_ns() - t0;
+        if (t != kDone) {
+            const uint32_t old = atomicAdd(a.state + t, 1u);   // PENDING -> ACTIVE
+            f = (old & ST_VISITED) == 0;
+            if (f) atomicOr(a.state + t, ST_VISITED);
+            __threadfence();
+        }
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    first = __shfl_sync(0xffffffffu, f, 0) != 0;
+    return t;
+}
+
+__device__ inline void flush_stats(const EngineArgs &a, const VisitStats &st, unsigned long long idle,
+                                   unsigned long long busy, int lane) {
+    if (lane == 0) {
+        atomicAdd(&a.hdr->visits, st.visits);
+        atomicAdd(&a.hdr->pops, st.pops);
+        atomicAdd(&a.hdr->seeds, st.seeds);
+        atomicAdd(&a.hdr->waves, st.waves);
+        atomicAdd(&a.hdr->idle_ns, idle);
+        atomicAdd(&a.hdr->busy_ns, busy);
+    }
+}
+
+// ---- kernels: one image of one pixel type and connectivity ---------------------------------------
 template <typename T, int CONN, int TH, int TW>
 __global__ void __launch_bounds__(kThreads) scan_kernel(EngineArgs a) {
     using TL = Tile<T, CONN, TH, TW>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const typename TL::Smem s = TL::carve(smem_raw + warp * TL::smem_per_warp(a.qcap));
+    uint8_t *wsmem = smem_raw + warp * TL::smem_per_warp(a.qcap);
     const uint32_t nworkers = gridDim.x * kWarpsPerCta;
-    for (uint32_t t = blockIdx.x * kWarpsPerCta + warp; t < a.ntiles; t += nworkers) {
-        const int ty = t / a.img.tiles_x, tx = t % a.img.tiles_x;
-        TL::clear_flags(s, lane);
-        TL::load_tile(a.img, s, ty, tx, lane);
-        TL::save_halo(s, lane);
-        bool bad = false;
-        for (int i = lane; i < TL::NPIX; i += 32) {
-            const int p = TL::pidx(i / TW + 1, i % TW);
-            bad |= TL::val(s.J[p]) > (uint32_t)s.I[p];
-        }
-        bad = __any_sync(0xffffffffu, bad);
-        unsigned long long rows = 0;
-        for (int k = 0; k < a.sweeps; k++) {
-            rows |= TL::sweep_raster(s, lane);
-            rows |= TL::sweep_antiraster(s, lane);
-        }
-        if (rows) TL::store_tile(a.img, s, ty, tx, rows, false, lane);
-        bool active = false;
-        for (int i = lane; i < TL::NPIX; i += 32) {
-            const int p = TL::pidx(i / TW + 1, i % TW);
-            uint32_t m = 0;
-#pragma unroll
-            for (int d = 0; d < TL::NDIR; d++) m = max(m, TL::val(s.J[p + TL::nb_off(d)]));
-            active |= min(m, (uint32_t)s.I[p]) > TL::val(s.J[p]);
-        }
-        active = __any_sync(0xffffffffu, active);
-        TL::notify_scan(s, lane);
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) {
-            if (bad) set_status(a.hdr, kErrPrecondition);
-            if (active) notify_tile(a, t);
-        }
-        TL::send_notifications(s, a, ty, tx, lane);
-        __syncwarp();
-    }
+    for (uint32_t t = blockIdx.x * kWarpsPerCta + warp; t < a.ntiles; t += nworkers)
+        scan_tile<T, CONN, TH, TW>(a, a.img0, t, wsmem, lane);
 }
 
-// ---- kernel 2: persistent drain (every warp is a worker) ----------------------------------------
 template <typename T, int CONN, int TH, int TW>
 __global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_kernel(EngineArgs a) {
     using TL = Tile<T, CONN, TH, TW>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const typename TL::Smem s = TL::carve(smem_raw + warp * TL::smem_per_warp(a.qcap));
+    uint8_t *wsmem = smem_raw + warp * TL::smem_per_warp(a.qcap);
     uint16_t *ovf = a.ovf + ((size_t)blockIdx.x * kWarpsPerCta + warp) * 2 * a.ovcap;
-    unsigned long long visits = 0, pops_total = 0, seeds_total = 0, waves_total = 0;
-    unsigned long long idle = 0, busy = 0, tmark = 0;
-#if IWPP_PHASE_TIMING
-    unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#endif
+    VisitStats st = {0, 0, 0, 0};
+    unsigned long long idle = 0, busy = 0;
     for (;;) {
-        uint32_t t = 0, first = 0;
-        if (lane == 0) {
-            tmark = globaltimer_ns();
-            t = pop_tile(a);
-            const unsigned long long now = globaltimer_ns();
-            idle += now - tmark;
-            tmark = now;
-            if (t != kDone) {
-                const uint32_t old = atomicAdd(a.state + t, 1u);   // PENDING -> ACTIVE
-                first = (old & ST_VISITED) == 0;
-                if (first) atomicOr(a.state + t, ST_VISITED);
-                __threadfence();
-            }
-        }
-        t = __shfl_sync(0xffffffffu, t, 0);
-        first = __shfl_sync(0xffffffffu, first, 0);
+        bool first;
+        const uint32_t t = acquire_tile(a, first, idle, lane);
         if (t == kDone) break;
-        const int ty = t / a.img.tiles_x, tx = t % a.img.tiles_x;
-#if IWPP_PHASE_TIMING
-        long long c0 = clock64();
-#define IWPP_PHASE(k) do { const long long c1 = clock64(); if (lane == 0) ph[k] += c1 - c0; c0 = c1; } while (0)
-#else
-#define IWPP_PHASE(k) do { } while (0)
-#endif
-        TL::clear_flags(s, lane);
-        TL::load_tile(a.img, s, ty, tx, lane);
-        TL::save_halo(s, lane);
-        IWPP_PHASE(0);
-        bool full = first != 0;
-        for (;;) {
-            unsigned long long rows = 0;
-            if (full) {
-                for (int k = 0; k < a.revisit_sweeps; k++) {
-                    rows |= TL::sweep_raster(s, lane);
-                    rows |= TL::sweep_antiraster(s, lane);
-                }
-            }
-            const uint32_t seeds = TL::seed_wave(s, a, ovf, full, rows, lane);
-            IWPP_PHASE(1);
-            uint32_t waves;
-            const uint32_t pops = TL::run_waves(s, a, ovf, seeds, rows, waves, lane);
-            IWPP_PHASE(2);
-            visits++;
-            pops_total += pops;
-            seeds_total += seeds;
-            waves_total += waves;
-            rows = (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)rows) |
-                   ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(rows >> 32)) << 32);
-            if (rows) TL::store_tile(a.img, s, ty, tx, rows, true, lane);
-            TL::notify_scan(s, lane);
-            IWPP_PHASE(3);
-            __threadfence();
-            __syncwarp();
-            IWPP_PHASE(4);
-            TL::send_notifications(s, a, ty, tx, lane);
-            IWPP_PHASE(5);
-            uint32_t redo = 0;
-            if (lane == 0) {
-                const uint32_t busy_st = ST_ACTIVE | ST_VISITED;
-                const uint32_t r = atomicCAS(a.state + t, busy_st, ST_VISITED);
-                if (r == busy_st) {
-                    __threadfence();
-                    atomicSub(&a.hdr->pending, 1u);
-                } else {
-                    atomicAnd(a.state + t, ~ST_PENDING);   // notified while ACTIVE: go again
-                    redo = 1;
-                }
-                __threadfence();
-                redo = redo && !fatal(a.hdr);
-            }
-            redo = __shfl_sync(0xffffffffu, redo, 0);
-            IWPP_PHASE(6);
-            if (!redo) {
-                if (lane == 0) busy += globaltimer_ns() - tmark;
-                break;
-            }
-            // Re-process: the interior in shared memory is what this warp stored; only the
-            // halo can have changed since.
-            TL::clear_flags(s, lane);
-            TL::load_halo_J(a.img, s, ty, tx, lane);
-            TL::save_halo(s, lane);
-            full = false;
-            IWPP_PHASE(7);
+        const unsigned long long b0 = globaltimer_ns();
+        visit_tile<T, CONN, TH, TW>(a, a.img0, t, first, wsmem, ovf, st, lane);
+        busy += globaltimer_ns() - b0;
+    }
+    flush_stats(a, st, idle, busy, lane);
+}
+
+// ---- kernels: a batch of images of mixed pixel types and connectivities -------------------------
+// Shared memory per warp is the largest of the four kinds' (they differ only in staging).
+template <int TH, int TW>
+__host__ __device__ inline size_t mixed_smem_per_warp(uint32_t qcap) {
+    const size_t a8 = Tile<uint8_t, 8, TH, TW>::smem_per_warp(qcap);
+    const size_t a16 = Tile<uint16_t, 8, TH, TW>::smem_per_warp(qcap);
+    return a8 > a16 ? a8 : a16;
+}
+
+template <int TH, int TW>
+__global__ void __launch_bounds__(kThreads) scan_mixed_kernel(EngineArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wsmem = smem_raw + warp * mixed_smem_per_warp<TH, TW>(a.qcap);
+    const uint32_t nworkers = gridDim.x * kWarpsPerCta;
+    for (uint32_t t = blockIdx.x * kWarpsPerCta + warp; t < a.ntiles; t += nworkers) {
+        const ImageView &im = image_of(a, t);
+        switch (im.kind) {
+            case 0: scan_tile<uint8_t, 4, TH, TW>(a, im, t, wsmem, lane); break;
+            case 1: scan_tile<uint16_t, 4, TH, TW>(a, im, t, wsmem, lane); break;
+            case 2: scan_tile<uint8_t, 8, TH, TW>(a, im, t, wsmem, lane); break;
+            default: scan_tile<uint16_t, 8, TH, TW>(a, im, t, wsmem, lane); break;
         }
-#undef IWPP_PHASE
     }
-    if (lane == 0) {
-        atomicAdd(&a.hdr->visits, visits);
-        atomicAdd(&a.hdr->pops, pops_total);
-        atomicAdd(&a.hdr->seeds, seeds_total);
-        atomicAdd(&a.hdr->waves, waves_total);
-        atomicAdd(&a.hdr->idle_ns, idle);
-        atomicAdd(&a.hdr->busy_ns, busy);
-#if IWPP_PHASE_TIMING
-        for (int k = 0; k < 8; k++) atomicAdd(&a.hdr->phase_cycles[k], ph[k]);
-#endif
+}
+
+template <int TH, int TW>
+__global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_mixed_kernel(EngineArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wsmem = smem_raw + warp * mixed_smem_per_warp<TH, TW>(a.qcap);
+    uint16_t *ovf = a.ovf + ((size_t)blockIdx.x * kWarpsPerCta + warp) * 2 * a.ovcap;
+    VisitStats st = {0, 0, 0, 0};
+    unsigned long long idle = 0, busy = 0;
+    for (;;) {
+        bool first;
+        const uint32_t t = acquire_tile(a, first, idle, lane);
+        if (t == kDone) break;
+        const unsigned long long b0 = globaltimer_ns();
+        const ImageView &im = image_of(a, t);
+        switch (im.kind) {
+            case 0: visit_tile<uint8_t, 4, TH, TW>(a, im, t, first, wsmem, ovf, st, lane); break;
+            case 1: visit_tile<uint16_t, 4, TH, TW>(a, im, t, first, wsmem, ovf, st, lane); break;
+            case 2: visit_tile<uint8_t, 8, TH, TW>(a, im, t, first, wsmem, ovf, st, lane); break;
+            default: visit_tile<uint16_t, 8, TH, TW>(a, im, t, first, wsmem, ovf, st, lane); break;
+        }
+        busy += globaltimer_ns() - b0;
     }
+    flush_stats(a, st, idle, busy, lane);
+}
+
+// Queue the PENDING tiles in schedule order (`order`, or tile id order) before the
+// persistent kernel starts: warp-aggregated tickets, no consumer runs yet. A tile is
+// claimed through the ST_QUEUED bit, so an order with repeated entries cannot queue a
+// tile twice; finalize_queue_kernel then queues any PENDING tile the order left out and
+// clears the bit.
+constexpr uint32_t ST_QUEUED = 8u;
+
+__device__ __forceinline__ void queue_warp(const EngineArgs &a, bool want, uint32_t t, int lane) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, want);
+    if (bal == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.hdr->tail, (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (want) a.queue[(base + __popc(bal & ((1u << lane) - 1u))) % a.ntiles] = t;
+}
+
+__global__ void __launch_bounds__(256) compact_kernel(EngineArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t nround = (a.ntiles + 31) / 32 * 32;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
+        uint32_t t = 0;
+        bool want = false;
+        if (i < a.ntiles) {
+            t = a.order ? a.order[i] : i;
+            if (t < a.ntiles && (a.state[t] & ST_PENDING) != 0)
+                want = (atomicOr(a.state + t, ST_QUEUED) & ST_QUEUED) == 0;
+        }
+        queue_warp(a, want, t, lane);
+    }
+}
+
+__global__ void __launch_bounds__(256) finalize_queue_kernel(EngineArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t nround = (a.ntiles + 31) / 32 * 32;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+        bool want = false;
+        if (t < a.ntiles) {
+            const uint32_t s = a.state[t];
+            want = (s & ST_PENDING) != 0 && (s & ST_QUEUED) == 0;
+            if (s & ST_QUEUED) a.state[t] = s & ~ST_QUEUED;
+        }
+        queue_warp(a, want, t, lane);
+    }
+}
+
+// Write a chunk of the batch's image table into the workspace (descriptors travel as
+// kernel parameters, so the call needs no host-to-device copy and can be captured).
+constexpr int kDescChunk = 32;
+struct DescChunk {
+    ImageView v[kDescChunk];
+    int first, count;
+};
+__global__ void upload_descs_kernel(ImageView *table, DescChunk c) {
+    const int i = threadIdx.x;
+    if (i < c.count) table[c.first + i] = c.v[i];
 }
 
 }  // namespace iwpp

@@ -1,0 +1,24 @@
+// iwpp_host.h — host-side helpers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/iwpp.h"
+
+namespace iwpp {
+int shape_index(int th, int tw);
+bool plan_valid(const iwpp_plan &p);
+void default_plan(iwpp_plan *p);
+size_t align256(size_t x);
+int device_sm_count();
+int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int conn, int op, int dtype,
+                    const iwpp_plan *plan, void *ws, size_t ws_bytes, cudaStream_t stream, int phases);
+size_t workspace_bytes(int64_t H, int64_t W, int dtype, const iwpp_plan *plan);
+int64_t batch_tiles(const iwpp_image *imgs, int n, const iwpp_plan &p, std::vector<uint32_t> *bases);
+size_t batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan);
+int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan, const uint32_t *order,
+                      const uint8_t *tile_sweeps, uint32_t *tile_work, void *ws, size_t ws_bytes,
+                      cudaStream_t stream);
+}  // namespace iwpp

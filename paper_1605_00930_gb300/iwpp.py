@@ -39,6 +39,13 @@ class Plan(ctypes.Structure):
         return f"Plan({self.as_dict()})"
 
 
+class Image(ctypes.Structure):
+    """iwpp_image: one image of a batch (device pointers)."""
+    _fields_ = [("marker_inout", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("H", ctypes.c_int64),
+                ("W", ctypes.c_int64), ("connectivity", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -61,6 +68,14 @@ _PROTOS = [
     ("iwpp_drain", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Plan),
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_batch_tile_count", ctypes.c_int64, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan)]),
+    ("iwpp_batch_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(Image), ctypes.c_int,
+                                                     ctypes.POINTER(Plan)]),
+    ("iwpp_reconstruct_batch", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_reconstruct_batch_sched", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("iwpp_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("iwpp_work_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -123,6 +138,27 @@ def iwpp_scan(marker_ptr, mask_ptr, H, W, conn, op, dtype, plan, ws_ptr, ws_byte
 def iwpp_drain(marker_ptr, mask_ptr, H, W, conn, op, dtype, plan, ws_ptr, ws_bytes, stream) -> int:
     return lib().iwpp_drain(marker_ptr, mask_ptr, H, W, conn, op, dtype,
                             ctypes.byref(plan) if plan is not None else None, ws_ptr, ws_bytes, stream)
+
+
+def _pp(plan):
+    return ctypes.byref(plan) if plan is not None else None
+
+
+def iwpp_batch_tile_count(imgs, plan: Plan | None = None) -> int:
+    return int(lib().iwpp_batch_tile_count(imgs, len(imgs), _pp(plan)))
+
+
+def iwpp_batch_workspace_bytes(imgs, plan: Plan | None = None) -> int:
+    return int(lib().iwpp_batch_workspace_bytes(imgs, len(imgs), _pp(plan)))
+
+
+def iwpp_reconstruct_batch(imgs, plan, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_reconstruct_batch(imgs, len(imgs), _pp(plan), ws_ptr, ws_bytes, stream)
+
+
+def iwpp_reconstruct_batch_sched(imgs, plan, order_ptr, sweeps_ptr, work_ptr, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_reconstruct_batch_sched(imgs, len(imgs), _pp(plan), order_ptr, sweeps_ptr, work_ptr,
+                                              ws_ptr, ws_bytes, stream)
 
 
 def iwpp_sync_status(ws_ptr, stream) -> int:
@@ -212,3 +248,51 @@ def reconstruct(marker, mask, conn: int = 8, op: str = "dilate", plan: Plan | No
     if st != 0:
         raise IwppError(st, "device status")
     return marker
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Batch:
+    """A fixed batch of (marker, mask, conn, op) torch CUDA tensors reconstructed in one
+    persistent launch; holds the descriptor array and a workspace sized for it."""
+
+    def __init__(self, items, plan: Plan | None = None, device=None):
+        self.items = list(items)
+        self.plan = plan
+        n = len(self.items)
+        self.descs = (Image * n)()
+        for i, (m, I, conn, op) in enumerate(self.items):
+            if m.shape != I.shape or m.dim() != 2 or m.dtype != I.dtype:
+                raise ValueError(f"image {i}: marker and mask must be equal 2-D tensors")
+            if not (m.is_cuda and I.is_cuda and m.is_contiguous() and I.is_contiguous()):
+                raise ValueError(f"image {i}: contiguous CUDA tensors required")
+            self.descs[i] = Image(m.data_ptr(), I.data_ptr(), m.shape[0], m.shape[1], int(conn), OPS[op],
+                                  _dtype_code(m), 0)
+        self.ntiles = iwpp_batch_tile_count(self.descs, plan)
+        if self.ntiles < 1:
+            raise IwppError(1, "iwpp_batch_tile_count")
+        nbytes = iwpp_batch_workspace_bytes(self.descs, plan)
+        if nbytes == 0:
+            raise IwppError(1, "iwpp_batch_workspace_bytes")
+        self.ws = alloc_workspace(nbytes, device or self.items[0][0].device)
+
+    @property
+    def pixels(self) -> int:
+        return sum(int(m.numel()) for m, _, _, _ in self.items)
+
+    def __call__(self, order=None, sweeps=None, work=None, stream=None) -> int:
+        """Enqueue the batch; order (int32/uint32 [ntiles]), sweeps (uint8 [ntiles]) and work
+        (int32 [2*ntiles], zeroed) are optional CUDA tensors. Returns the host status."""
+        ws = ctypes.c_void_p(self.ws.data_ptr())
+        if order is None and sweeps is None and work is None:
+            return iwpp_reconstruct_batch(self.descs, self.plan, ws, self.ws.numel(), _stream_handle(stream))
+        return iwpp_reconstruct_batch_sched(self.descs, self.plan, _ptr(order), _ptr(sweeps), _ptr(work), ws,
+                                            self.ws.numel(), _stream_handle(stream))
+
+    def status(self, stream=None) -> int:
+        return iwpp_sync_status(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
+
+    def counters(self, stream=None):
+        return iwpp_work_counters(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))

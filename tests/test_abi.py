@@ -91,3 +91,17 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         mod.lib()
     importlib.reload(m)
+
+
+def test_batch_tile_count_is_host_only(iwpp):
+    P = iwpp.Image
+    imgs = (P * 3)()
+    buf = (ctypes.c_uint8 * 64)()
+    a16 = (ctypes.addressof(buf) + 15) // 16 * 16
+    for i, (H, W) in enumerate([(1, 1), (33, 64), (100, 31)]):
+        imgs[i] = P(a16, a16, H, W, 8, 0, 0, 0)
+    p = iwpp.iwpp_default_plan()
+    p.tile_h, p.tile_w = 32, 32
+    assert iwpp.iwpp_batch_tile_count(imgs, p) == 1 + 2 * 2 + 4 * 1
+    imgs[1].connectivity = 6
+    assert iwpp.iwpp_batch_tile_count(imgs, p) == -1

@@ -32,7 +32,7 @@
  *     unspecified.
  *   - All calls are asynchronous on `stream` (a cudaStream_t; NULL = the
  *     legacy default stream) and perform no host synchronisation, except
- *     iwpp_sync_status and the iwpp_autotune helper.
+ *     iwpp_sync_status, iwpp_work_counters and iwpp_autotune_batch.
  */
 #ifndef IWPP_H
 #define IWPP_H
@@ -198,6 +198,36 @@ IWPP_API int iwpp_reconstruct_batch_sched(const iwpp_image *imgs, int n, const i
                                           const uint32_t *tile_order, const uint8_t *tile_sweeps,
                                           uint32_t *tile_work, void *workspace, size_t ws_bytes,
                                           void *stream);
+
+/*
+ * ---- CUDA graphs and autotuning (host runtime) ----------------------------------
+ * iwpp_batch_graph_create captures one batch call (static schedule, or the device
+ * schedule arrays given) into an executable CUDA graph: the descriptors, plan,
+ * workspace and schedule pointers are frozen into it. Each iwpp_graph_launch then
+ * reruns the whole batch with one launch on `stream` (restore the markers first:
+ * the result overwrites them). Graph creation allocates host-side graph objects and
+ * synchronises nothing on the caller's streams; destroy with iwpp_graph_destroy.
+ */
+typedef struct iwpp_graph_s *iwpp_graph;
+IWPP_API int iwpp_batch_graph_create(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                     const uint32_t *tile_order, const uint8_t *tile_sweeps,
+                                     void *workspace, size_t ws_bytes, iwpp_graph *out);
+IWPP_API int iwpp_graph_launch(iwpp_graph graph, void *stream);
+IWPP_API int iwpp_graph_destroy(iwpp_graph graph);
+
+/*
+ * Autotuner: picks the tile shape, sweep count and shared queue capacity of
+ * *plan_inout by timing candidate plans on the batch itself (coordinate descent
+ * from the given plan; best of `reps` runs each; CUDA events on `stream`). The
+ * markers are backed up first and restored after every trial and at the end, so
+ * the batch's images are unchanged on return. This call allocates device memory
+ * (backups, a workspace) and synchronises `stream`. cache_path (may be NULL) is a
+ * text file of previous results keyed by GPU name and a coarse batch signature; a
+ * hit returns the cached plan without timing (best_ms = 0). *best_ms (may be
+ * NULL) receives the winning time.
+ */
+IWPP_API int iwpp_autotune_batch(const iwpp_image *imgs, int n, iwpp_plan *plan_inout, int reps,
+                                 const char *cache_path, void *stream, float *best_ms);
 
 /*
  * Work counters of the last call (single image or batch) that used `workspace`: tile

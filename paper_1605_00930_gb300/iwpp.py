@@ -76,6 +76,14 @@ _PROTOS = [
     ("iwpp_reconstruct_batch_sched", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_batch_graph_create", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    ("iwpp_graph_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("iwpp_graph_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("iwpp_autotune_batch", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                           ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_float)]),
     ("iwpp_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("iwpp_work_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -161,6 +169,32 @@ def iwpp_reconstruct_batch_sched(imgs, plan, order_ptr, sweeps_ptr, work_ptr, ws
                                               ws_ptr, ws_bytes, stream)
 
 
+def iwpp_batch_graph_create(imgs, plan, order_ptr, sweeps_ptr, ws_ptr, ws_bytes):
+    g = ctypes.c_void_p()
+    rc = lib().iwpp_batch_graph_create(imgs, len(imgs), _pp(plan), order_ptr, sweeps_ptr, ws_ptr, ws_bytes,
+                                       ctypes.byref(g))
+    if rc != 0:
+        raise IwppError(rc, "iwpp_batch_graph_create")
+    return g
+
+
+def iwpp_graph_launch(g, stream) -> int:
+    return lib().iwpp_graph_launch(g, stream)
+
+
+def iwpp_graph_destroy(g) -> int:
+    return lib().iwpp_graph_destroy(g)
+
+
+def iwpp_autotune_batch(imgs, plan: Plan, reps: int = 2, cache_path: str | None = None, stream=None):
+    ms = ctypes.c_float(0)
+    rc = lib().iwpp_autotune_batch(imgs, len(imgs), ctypes.byref(plan), int(reps),
+                                   cache_path.encode() if cache_path else None, stream, ctypes.byref(ms))
+    if rc != 0:
+        raise IwppError(rc, "iwpp_autotune_batch")
+    return plan, float(ms.value)
+
+
 def iwpp_sync_status(ws_ptr, stream) -> int:
     return lib().iwpp_sync_status(ws_ptr, stream)
 
@@ -235,6 +269,43 @@ class Reconstructor:
     def counters(self, stream=None):
         return iwpp_work_counters(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
 
+    def graph(self, order=None, sweeps=None) -> "Graph":
+        """Capture this batch (with an optional device schedule) into a CUDA graph."""
+        g = iwpp_batch_graph_create(self.descs, self.plan, _ptr(order), _ptr(sweeps),
+                                    ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel())
+        return Graph(g, (order, sweeps))
+
+    def autotune(self, reps: int = 2, cache_path: str | None = None, stream=None):
+        """Pick this batch's plan with the library's autotuner (markers are restored). The
+        workspace is re-sized for the chosen plan."""
+        plan = Plan.from_buffer_copy(self.plan) if self.plan is not None else iwpp_default_plan()
+        plan, ms = iwpp_autotune_batch(self.descs, plan, reps, cache_path, _stream_handle(stream))
+        self.plan = plan
+        self.ntiles = iwpp_batch_tile_count(self.descs, plan)
+        nbytes = iwpp_batch_workspace_bytes(self.descs, plan)
+        if nbytes > self.ws.numel():
+            self.ws = alloc_workspace(nbytes, self.ws.device)
+        return plan, ms
+
+
+class Graph:
+    """An executable CUDA graph of one batch call (see iwpp_batch_graph_create)."""
+
+    def __init__(self, handle, keepalive):
+        self.handle = handle
+        self._keep = keepalive
+
+    def launch(self, stream=None) -> int:
+        return iwpp_graph_launch(self.handle, _stream_handle(stream))
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                iwpp_graph_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
 
 def reconstruct(marker, mask, conn: int = 8, op: str = "dilate", plan: Plan | None = None, stream=None):
     """Reconstruct ``mask`` from ``marker`` in place on ``marker`` (torch CUDA tensors,
@@ -296,3 +367,40 @@ class Batch:
 
     def counters(self, stream=None):
         return iwpp_work_counters(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
+
+    def graph(self, order=None, sweeps=None) -> "Graph":
+        """Capture this batch (with an optional device schedule) into a CUDA graph."""
+        g = iwpp_batch_graph_create(self.descs, self.plan, _ptr(order), _ptr(sweeps),
+                                    ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel())
+        return Graph(g, (order, sweeps))
+
+    def autotune(self, reps: int = 2, cache_path: str | None = None, stream=None):
+        """Pick this batch's plan with the library's autotuner (markers are restored). The
+        workspace is re-sized for the chosen plan."""
+        plan = Plan.from_buffer_copy(self.plan) if self.plan is not None else iwpp_default_plan()
+        plan, ms = iwpp_autotune_batch(self.descs, plan, reps, cache_path, _stream_handle(stream))
+        self.plan = plan
+        self.ntiles = iwpp_batch_tile_count(self.descs, plan)
+        nbytes = iwpp_batch_workspace_bytes(self.descs, plan)
+        if nbytes > self.ws.numel():
+            self.ws = alloc_workspace(nbytes, self.ws.device)
+        return plan, ms
+
+
+class Graph:
+    """An executable CUDA graph of one batch call (see iwpp_batch_graph_create)."""
+
+    def __init__(self, handle, keepalive):
+        self.handle = handle
+        self._keep = keepalive
+
+    def launch(self, stream=None) -> int:
+        return iwpp_graph_launch(self.handle, _stream_handle(stream))
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                iwpp_graph_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None

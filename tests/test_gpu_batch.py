@@ -118,3 +118,52 @@ def test_mixed_batch_full_size(iw, oracle_lib):
     exps = oracle_lib.reconstruct_many([(c.marker, c.mask, c.conn, c.op) for c in cases])
     for i, (got, exp) in enumerate(zip(outs, exps)):
         assert np.array_equal(got, exp), f"image {i} differs"
+
+
+def test_batch_graph_replays_bit_exact(iw, oracle_lib):
+    cases = _mixed_cases(11, 16)
+    items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
+    init = [m.clone() for m, _, _, _ in items]
+    B = iw.Batch(items)
+    g = B.graph()
+    for _ in range(2):
+        for (m, _, _, _), m0 in zip(items, init):
+            m.copy_(m0)
+        assert g.launch() == 0
+        assert B.status() == 0
+        _check(oracle_lib, cases, [m.cpu().numpy() for m, _, _, _ in items])
+
+
+def test_batch_call_captures_in_torch_graph(iw, oracle_lib):
+    cases = _mixed_cases(12, 6)
+    items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
+    init = [m.clone() for m, _, _, _ in items]
+    B = iw.Batch(items)
+    assert B() == 0 and B.status() == 0          # warm-up outside capture
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            assert B(stream=s) == 0
+    for (m, _, _, _), m0 in zip(items, init):
+        m.copy_(m0)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert B.status() == 0
+    _check(oracle_lib, cases, [m.cpu().numpy() for m, _, _, _ in items])
+
+
+def test_autotune_restores_markers_and_caches(iw, oracle_lib, tmp_path):
+    cases = _mixed_cases(13, 10, max_side=500)
+    items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
+    B = iw.Batch(items)
+    cache = str(tmp_path / "tune.txt")
+    plan, ms = B.autotune(reps=1, cache_path=cache)
+    assert ms > 0 and iw.iwpp_tile_shape_supported(plan.tile_h, plan.tile_w)
+    for (m, _, _, _), c in zip(items, cases):
+        assert np.array_equal(m.cpu().numpy(), c.marker)       # untouched by tuning
+    assert B() == 0 and B.status() == 0
+    _check(oracle_lib, cases, [m.cpu().numpy() for m, _, _, _ in items])
+    # a second tuning of the same batch signature is a cache hit
+    plan2, ms2 = iw.iwpp_autotune_batch(B.descs, iw.iwpp_default_plan(), 1, cache)
+    assert ms2 == 0.0 and plan2.as_dict()["tile_h"] == plan.tile_h and plan2.sweeps == plan.sweeps

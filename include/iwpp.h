@@ -230,6 +230,79 @@ IWPP_API int iwpp_autotune_batch(const iwpp_image *imgs, int n, iwpp_plan *plan_
                                  const char *cache_path, void *stream, float *best_ms);
 
 /*
+ * ---- Learned work estimator (schedule of a batch) ---------------------------------
+ * Every image is cut into IWPP_FEATURE_BLOCK x IWPP_FEATURE_BLOCK blocks (the last
+ * ones partial), numbered image by image, row-major. Per block, IWPP_NFEAT float
+ * features, in the dilation domain (both images complemented for erosion),
+ * d = max(I - J, 0), d8 = d (u8) or d >> 8 (u16):
+ *   [0..7]   fractions of the block with d8 == 0, d8 == 1, 2..3, 4..7, 8..15,
+ *            16..31, 32..63, >= 64
+ *   [8]      fraction with J == I and J > 0 (seeds)
+ *   [9]      fraction with |I(p)-I(p+x)| + |I(p)-I(p+y)| > 16 * MAXV / 255
+ *            (a neighbour outside the block contributes 0)
+ *   [10..14] mean(I), std(I), mean(J), std(J), mean(d), each / MAXV
+ *   [15]     log2(pixels in the block) / 12
+ * The MLP is 16 -> 64 -> 64 -> 2 with ReLU, FP32, IWPP_MLP_PARAMS parameters in
+ * one flat device array: W1[16][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]
+ * (y = x W + b). Output 0 predicts log(1 + wave-queue pops) of the block, output
+ * 1 the raster / anti-raster sweep pairs to run on its tiles.
+ * The paper has no learned schedule; none of these calls can change a
+ * reconstruction result, they only order the work.
+ */
+#define IWPP_FEATURE_BLOCK 64
+#define IWPP_NFEAT 16
+#define IWPP_MLP_PARAMS 5378
+
+/* Feature blocks of a batch, or -1 for a bad argument (host-only). */
+IWPP_API int64_t iwpp_batch_block_count(const iwpp_image *imgs, int n);
+
+/* Bytes of the scheduling workspace for this batch and plan (0 for a bad argument;
+ * the plan's tile sides must divide IWPP_FEATURE_BLOCK). Caller-owned device memory,
+ * 256-byte aligned. */
+IWPP_API size_t iwpp_sched_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan);
+
+/* Features of every block of the batch into feats (device, float[nblocks][16]). */
+IWPP_API int iwpp_batch_features(const iwpp_image *imgs, int n, float *feats, void *sched_ws,
+                                 size_t sws_bytes, void *stream);
+
+/* Y[N][2] = MLP(params, X[N][16]) (device arrays). */
+IWPP_API int iwpp_mlp_forward(const float *params, const float *X, int64_t N, float *Y, void *stream);
+
+/*
+ * Trains the MLP in place: `epochs` passes over the N samples (X[N][16] inputs,
+ * T[N][2] targets, device arrays) in minibatches of `batch` (a fresh affine
+ * permutation of the samples per epoch, drawn from `seed`), loss
+ * (1/B) sum (w0 (y0 - t0)^2 + w1 (y1 - t1)^2), Adam with learning rate lr (moments
+ * adam_m, adam_v: float[IWPP_MLP_PARAMS], zeroed before the first step; step0 = the
+ * number of Adam steps already taken). grad: float[IWPP_MLP_PARAMS] scratch,
+ * zeroed by the caller once; it is left zeroed.
+ */
+IWPP_API int iwpp_mlp_train(float *params, float *adam_m, float *adam_v, float *grad, const float *X,
+                            const float *T, int64_t N, int epochs, int batch, float lr, float w0, float w1,
+                            uint64_t seed, int64_t step0, void *stream);
+
+/*
+ * Schedule from per-block predictions preds[nblocks][2] (device): tile_order
+ * (uint32[ntiles]) lists the batch's tiles by decreasing predicted work (output 0,
+ * bucketed in steps of 1/64), tile_sweeps (uint8[ntiles]) = output 1 of the tile's
+ * block, rounded and clamped to 0..8. Ready for iwpp_reconstruct_batch_sched.
+ */
+IWPP_API int iwpp_schedule_from_predictions(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                            const float *preds, uint32_t *tile_order, uint8_t *tile_sweeps,
+                                            void *sched_ws, size_t sws_bytes, void *stream);
+
+/* Features, MLP inference and schedule in one call (all on `stream`, no host sync). */
+IWPP_API int iwpp_schedule_learned(const iwpp_image *imgs, int n, const iwpp_plan *plan, const float *params,
+                                   uint32_t *tile_order, uint8_t *tile_sweeps, void *sched_ws,
+                                   size_t sws_bytes, void *stream);
+
+/* Per-tile work from iwpp_reconstruct_batch_sched summed into blocks:
+ * block_work[b] = pops, block_work[nblocks + b] = SM cycles (caller-zeroed uint64). */
+IWPP_API int iwpp_tile_work_to_blocks(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                      const uint32_t *tile_work, unsigned long long *block_work,
+                                      void *sched_ws, size_t sws_bytes, void *stream);
+
+/*
  * Work counters of the last call (single image or batch) that used `workspace`: tile
  * visits by the persistent kernel, wave-queue entries processed (pops),
  * entries created by the visits' initial scans (seeds), wave steps run, and

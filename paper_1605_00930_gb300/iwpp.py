@@ -84,6 +84,25 @@ _PROTOS = [
     ("iwpp_autotune_batch", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
                                            ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_float)]),
+    ("iwpp_batch_block_count", ctypes.c_int64, [ctypes.POINTER(Image), ctypes.c_int]),
+    ("iwpp_sched_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan)]),
+    ("iwpp_batch_features", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_mlp_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    ("iwpp_mlp_train", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                      ctypes.c_int64, ctypes.c_void_p]),
+    ("iwpp_schedule_from_predictions", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_schedule_learned", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_tile_work_to_blocks", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                ctypes.c_void_p]),
     ("iwpp_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("iwpp_work_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -152,6 +171,10 @@ def _pp(plan):
     return ctypes.byref(plan) if plan is not None else None
 
 
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
 def iwpp_batch_tile_count(imgs, plan: Plan | None = None) -> int:
     return int(lib().iwpp_batch_tile_count(imgs, len(imgs), _pp(plan)))
 
@@ -193,6 +216,56 @@ def iwpp_autotune_batch(imgs, plan: Plan, reps: int = 2, cache_path: str | None 
     if rc != 0:
         raise IwppError(rc, "iwpp_autotune_batch")
     return plan, float(ms.value)
+
+
+NFEAT = 16
+MLP_PARAMS = 5378
+FEATURE_BLOCK = 64
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise IwppError(rc, what)
+
+
+def iwpp_batch_block_count(imgs) -> int:
+    return int(lib().iwpp_batch_block_count(imgs, len(imgs)))
+
+
+def iwpp_sched_workspace_bytes(imgs, plan=None) -> int:
+    return int(lib().iwpp_sched_workspace_bytes(imgs, len(imgs), _pp(plan)))
+
+
+def iwpp_batch_features(imgs, feats, sws, stream=None):
+    _check(lib().iwpp_batch_features(imgs, len(imgs), _ptr(feats), _ptr(sws), sws.numel(), _stream_handle(stream)),
+           "iwpp_batch_features")
+
+
+def iwpp_mlp_forward(params, X, Y, stream=None):
+    _check(lib().iwpp_mlp_forward(_ptr(params), _ptr(X), X.shape[0], _ptr(Y), _stream_handle(stream)),
+           "iwpp_mlp_forward")
+
+
+def iwpp_mlp_train(params, m, v, grad, X, T, epochs, batch, lr, w0=1.0, w1=1.0, seed=0, step0=0, stream=None):
+    _check(lib().iwpp_mlp_train(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), _ptr(X), _ptr(T), X.shape[0],
+                                int(epochs), int(batch), float(lr), float(w0), float(w1), int(seed), int(step0),
+                                _stream_handle(stream)), "iwpp_mlp_train")
+
+
+def iwpp_schedule_from_predictions(imgs, plan, preds, order, sweeps, sws, stream=None):
+    _check(lib().iwpp_schedule_from_predictions(imgs, len(imgs), _pp(plan), _ptr(preds), _ptr(order), _ptr(sweeps),
+                                                _ptr(sws), sws.numel(), _stream_handle(stream)),
+           "iwpp_schedule_from_predictions")
+
+
+def iwpp_schedule_learned(imgs, plan, params, order, sweeps, sws, stream=None):
+    _check(lib().iwpp_schedule_learned(imgs, len(imgs), _pp(plan), _ptr(params), _ptr(order), _ptr(sweeps),
+                                       _ptr(sws), sws.numel(), _stream_handle(stream)), "iwpp_schedule_learned")
+
+
+def iwpp_tile_work_to_blocks(imgs, plan, tile_work, block_work, sws, stream=None):
+    _check(lib().iwpp_tile_work_to_blocks(imgs, len(imgs), _pp(plan), _ptr(tile_work), _ptr(block_work),
+                                          _ptr(sws), sws.numel(), _stream_handle(stream)), "iwpp_tile_work_to_blocks")
 
 
 def iwpp_sync_status(ws_ptr, stream) -> int:
@@ -319,10 +392,6 @@ def reconstruct(marker, mask, conn: int = 8, op: str = "dilate", plan: Plan | No
     if st != 0:
         raise IwppError(st, "device status")
     return marker
-
-
-def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
 class Batch:

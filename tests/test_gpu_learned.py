@@ -1,0 +1,151 @@
+"""GPU parity of the learned schedule: feature kernel and MLP kernels against the
+float64 oracle; schedule validity; and the learned-scheduled batch bit-exact."""
+import numpy as np
+import pytest
+
+from oracle import features as ofeat
+from oracle import mlp as omlp
+from paper_1605_00930_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def iw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_00930_gb300 import build
+    build.build()
+    from paper_1605_00930_gb300 import iwpp
+    iwpp.lib()
+    return iwpp
+
+
+def _cases(seed, n, side=260):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        H, W = int(rng.integers(1, side)), int(rng.integers(1, side))
+        is16 = bool(rng.integers(0, 2))
+        f = synth.blob_field_u8(H, W, max(1, H * W // 2500), rng)
+        mask = synth.to_u16(f) if is16 else f
+        if i % 2 == 0:
+            out.append(synth.Case(synth.hdome_marker(mask, int(rng.integers(5, 50)) * (257 if is16 else 1)), mask,
+                                  8, "dilate"))
+        else:
+            out.append(synth.Case(synth.fillholes_marker(mask), mask, 4, "erode"))
+    return out
+
+
+def _items(cases):
+    return [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
+
+
+def test_features_match_oracle(iw):
+    from paper_1605_00930_gb300 import learned
+    cases = _cases(21, 9)
+    got = learned.features(_items(cases)).cpu().numpy()
+    exp = ofeat.batch_features(cases)
+    assert got.shape == exp.shape
+    # counts are exact integers; moments are rounded once to float32
+    np.testing.assert_allclose(got, exp, rtol=1e-6, atol=1e-7)
+
+
+def test_mlp_forward_matches_oracle(iw):
+    rng = np.random.default_rng(2)
+    p = omlp.init_params(4).astype(np.float32)
+    X = rng.random((1000, 16)).astype(np.float32)
+    Y = torch.empty((1000, 2), dtype=torch.float32, device="cuda")
+    iw.iwpp_mlp_forward(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(), Y)
+    exp = omlp.forward(p.astype(np.float64), X.astype(np.float64))
+    # fp32 sums of <= 64 products of O(1) terms
+    np.testing.assert_allclose(Y.cpu().numpy(), exp, rtol=1e-4, atol=1e-4)
+
+
+def test_mlp_gradient_matches_oracle(iw):
+    """One full-batch Adam step with lr = 0 leaves m = (1 - beta1) * gradient."""
+    rng = np.random.default_rng(3)
+    p = omlp.init_params(5).astype(np.float32)
+    X = rng.random((700, 16)).astype(np.float32)
+    T = rng.normal(size=(700, 2)).astype(np.float32)
+    dp = torch.from_numpy(p).cuda()
+    m = torch.zeros(iw.MLP_PARAMS, device="cuda")
+    v = torch.zeros_like(m)
+    g = torch.zeros_like(m)
+    iw.iwpp_mlp_train(dp, m, v, g, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), 1, 700, 0.0, 1.0, 0.5)
+    got = m.cpu().numpy() / 0.1
+    exp = omlp.grad(p.astype(np.float64), X.astype(np.float64), T.astype(np.float64), (1.0, 0.5))
+    np.testing.assert_allclose(got, exp, rtol=2e-3, atol=2e-5 * np.abs(exp).max())
+    assert np.array_equal(dp.cpu().numpy(), p)          # lr = 0: parameters unchanged
+    assert np.all(g.cpu().numpy() == 0)                  # gradient consumed
+
+
+def test_training_reduces_loss(iw):
+    rng = np.random.default_rng(4)
+    X = rng.random((4000, 16)).astype(np.float32)
+    T = np.stack([3 * X[:, 0] + X[:, 5], np.round(4 * X[:, 2])], 1).astype(np.float32)
+    from paper_1605_00930_gb300 import learned
+    s = learned.LearnedScheduler(learned.init_params(1))
+    p0 = s.params.cpu().numpy().astype(np.float64)
+    s.train(X, T, epochs=20, batch=256, lr=3e-3, w=(1.0, 1.0))
+    p1 = s.params.cpu().numpy().astype(np.float64)
+    assert omlp.loss(p1, X, T) < 0.2 * omlp.loss(p0, X, T)
+
+
+def test_schedule_is_a_largest_first_permutation(iw):
+    cases = _cases(22, 7)
+    items = _items(cases)
+    B = iw.Batch(items)
+    nb = iw.iwpp_batch_block_count(B.descs)
+    rng = np.random.default_rng(9)
+    preds = np.stack([rng.uniform(0, 12, nb), rng.uniform(-2, 11, nb)], 1).astype(np.float32)
+    sws = iw.alloc_workspace(iw.iwpp_sched_workspace_bytes(B.descs))
+    order = torch.empty(B.ntiles, dtype=torch.int32, device="cuda")
+    sweeps = torch.empty(B.ntiles, dtype=torch.uint8, device="cuda")
+    iw.iwpp_schedule_from_predictions(B.descs, None, torch.from_numpy(preds).cuda(), order, sweeps, sws)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(B.ntiles))
+    # tile -> block map (32 x 32 tiles inside 64 x 64 blocks), image by image
+    blk = []
+    bbase = 0
+    for c in cases:
+        H, W = c.mask.shape
+        tx, ty = (W + 31) // 32, (H + 31) // 32
+        nbx = (W + 63) // 64
+        for t in range(tx * ty):
+            blk.append(bbase + (t // tx) // 2 * nbx + (t % tx) // 2)
+        bbase += nbx * ((H + 63) // 64)
+    blk = np.array(blk)
+    keys = np.clip((preds[blk, 0] * 64).astype(np.int64), 0, 1023)
+    assert np.all(np.diff(keys[o]) <= 0)
+    np.testing.assert_array_equal(sweeps.cpu().numpy(), np.clip(np.rint(preds[blk, 1]), 0, 8))
+
+
+def test_learned_batch_is_bit_exact(iw, oracle_lib):
+    from paper_1605_00930_gb300 import learned
+    cases = _cases(23, 12, side=400)
+    items = _items(cases)
+    sch = learned.LearnedScheduler(learned.init_params(3))
+    B = iw.Batch(items)
+    order, sweeps = sch.schedule(B)
+    assert B(order=order, sweeps=sweeps) == 0
+    assert B.status() == 0
+    for c, (m, _, _, _) in zip(cases, items):
+        assert np.array_equal(m.cpu().numpy(), oracle_lib.reconstruct(c.marker, c.mask, c.conn, c.op))
+
+
+def test_block_labels_and_roundtrip(iw, tmp_path):
+    from paper_1605_00930_gb300 import learned
+    cases = _cases(24, 4, side=300)
+    items = _items(cases)
+    lw, best, cyc = learned.block_labels(items)
+    assert lw.shape == best.shape and np.all(lw >= 0) and set(np.unique(best)) <= set(learned.SWEEP_OPTIONS)
+    for (m, _, _, _), c in zip(items, cases):
+        assert np.array_equal(m.cpu().numpy(), c.marker)   # markers restored
+    s = learned.LearnedScheduler(learned.init_params(2), meta={"note": "t"})
+    s.save(str(tmp_path / "w.bin"))
+    s2 = learned.LearnedScheduler.load(str(tmp_path / "w.bin"))
+    assert s2 is not None and torch.equal(s.params, s2.params)
+    (tmp_path / "w.bin").write_bytes(b"junk")
+    assert learned.LearnedScheduler.load(str(tmp_path / "w.bin")) is None

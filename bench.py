@@ -166,13 +166,15 @@ def run_ours(args, rank: int, world: int):
             m.copy_(m0)
         flush.fill_(1)
 
-    # correctness of the timed configuration (checked once against the oracle on rank 0)
+    # one untimed run of the timed configuration; its output is compared with the CPU
+    # oracle's in the CPU-baseline leg below
     prep()
     step()
     for (m0, I, m, R, conn, op) in dev_cases:
         st = R.status(stream)
         if st != 0:
             raise RuntimeError(f"device status {iwpp.STATUS.get(st)}")
+    first_outputs = [m.cpu().numpy() for (m0, I, m, R, conn, op) in dev_cases]
     for _ in range(args.warmup):
         prep()
         step()
@@ -244,7 +246,8 @@ def run_ours(args, rank: int, world: int):
     alg_bytes = 3 * s * cases[0][1].size   # compulsory bytes of one reconstruction: read J, I, write J
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     traffic = _traffic_from_profiles(dominant)
-    cpu = cpu_baseline(cases) if rank == 0 and world == 1 and not args.no_cpu else None
+    cpu = cpu_baseline(cases, first_outputs) if rank == 0 and world == 1 and not args.no_cpu else None
+    forms = run_forms(args, dev) if rank == 0 and world == 1 and not args.quick else None
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -266,25 +269,146 @@ def run_ours(args, rank: int, world: int):
         "gpu_launches": 2 * nl * args.steps,
         "clocks": cs.summary(t0, t1),
         "cpu_baseline": cpu,
+        "forms": forms,
     }
     return out
 
 
-def cpu_baseline(cases, budget_s: float = 12.0):
+def cpu_baseline(cases, gpu_outputs=None, budget_s: float = 12.0):
+    """Times the CPU oracle on the workload; its first pass is also compared, pixel for
+    pixel, with the GPU's untimed first run."""
     import oracle
     oracle.build()
     done_px, t0 = 0, time.perf_counter()
     reps = 0
+    exact = None
     while True:
-        for marker, mask, conn, op in cases:
-            oracle.reconstruct(marker, mask, conn, op)
+        for k, (marker, mask, conn, op) in enumerate(cases):
+            r = oracle.reconstruct(marker, mask, conn, op)
+            if reps == 0 and gpu_outputs is not None:
+                exact = (exact is not False) and bool(np.array_equal(r, gpu_outputs[k]))
             done_px += mask.size
         reps += 1
         if time.perf_counter() - t0 > budget_s or reps >= 5:
             break
     dt = time.perf_counter() - t0
     return {"value": round(done_px / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full pass(es) of the workload ({done_px} px), single-threaded C oracle"}
+            "sample": f"{reps} full pass(es) of the workload ({done_px} px), single-threaded C oracle",
+            "gpu_output_bit_exact": exact}
+
+
+def _dev_items(cases, dev):
+    import torch
+    items, init = [], []
+    for c in cases:
+        m0 = torch.from_numpy(c.marker).to(dev)
+        items.append((m0.clone(), torch.from_numpy(c.mask).to(dev), c.conn, c.op))
+        init.append(m0)
+    return items, init
+
+
+def _timed(run, items, init, flush, reps, stream):
+    """Median and all per-rep times (ms) of `run`, markers restored and L2 flushed
+    before every rep, CUDA events on `stream` around the run only."""
+    import torch
+    ts = []
+    for r in range(reps + 1):
+        for (m, _, _, _), m0 in zip(items, init):
+            m.copy_(m0)
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r > 0:
+            ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), ts
+
+
+def run_forms(args, dev):
+    """Plain per-image form against the batched (one persistent CUDA-graph launch,
+    autotuned plan) and batched + learned-schedule forms, on the sparse-seed 16384^2
+    image, the 256-image uneven batch and the 512-image batch; outputs of every form
+    are checked equal to the plain form's."""
+    import torch
+    from paper_1605_00930_gb300 import iwpp, learned, synth
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    reps = max(1, args.form_reps)
+    out = {}
+    t_start = time.time()
+
+    # learned estimator: labels from runs of the 512^2, 4096^2 (conn 8 and 4) and 16384^2 workloads
+    c1, c2 = synth.noise_blur_case(), synth.tissue_case()
+    c2b = synth.Case(c2.marker, c2.mask, 4, "dilate")
+    c3 = synth.sparse_seed_case()
+    sets = [_dev_items([c], dev)[0] for c in (c1, c2, c2b, c3)]
+    t0 = time.time()
+    sch, report = learned.train_from_workloads(sets, n_samples=50000, epochs=60)
+    report["seconds"] = round(time.time() - t0, 2)
+    out["estimator"] = report
+    del sets
+
+    def plain_loop(items):
+        Rs = [iwpp.Reconstructor(m.shape[0], m.shape[1], m.dtype, None, dev) for m, _, _, _ in items]
+
+        def run():
+            for R, (m, I, conn, op) in zip(Rs, items):
+                if R(m, I, conn, op, stream) != 0:
+                    raise RuntimeError("plain call failed")
+        return run, Rs
+
+    def batched(items, plan, learned_sched):
+        B = iwpp.Batch(items, plan)
+        if learned_sched:
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                order, sweeps = sch.schedule(B, s)        # allocate the schedule buffers first
+                with torch.cuda.graph(g, stream=s):
+                    sch.schedule(B, s)
+                    if B(order=order, sweeps=sweeps, stream=s) != 0:
+                        raise RuntimeError("batch call failed")
+            stream.wait_stream(s)
+            return (lambda: g.replay()), B
+        G = B.graph()
+        return (lambda: G.launch(stream)), (B, G)
+
+    def compare(name, cases, tune):
+        items, init = _dev_items(cases, dev)
+        px = sum(c.mask.size for c in cases)
+        res = {"images": len(cases), "pixels": px}
+        run, keep = plain_loop(items)
+        ms, _ = _timed(run, items, init, flush, reps, stream)
+        ref = [m.cpu().numpy() for m, _, _, _ in items]
+        res["plain_ms"] = round(ms, 3)
+        res["plain_gpx_s"] = round(px / ms / 1e6, 3)
+        plan = iwpp.iwpp_default_plan()
+        if tune:
+            Bt = iwpp.Batch(items, plan)
+            plan, tms = Bt.autotune(reps=1)
+            res["autotuned_plan"] = plan.as_dict()
+            del Bt
+        for form, lsch in (("batched_static", False), ("batched_learned", True)):
+            run, keep = batched(items, plan, lsch)
+            ms, _ = _timed(run, items, init, flush, reps, stream)
+            same = all(np.array_equal(m.cpu().numpy(), r) for (m, _, _, _), r in zip(items, ref))
+            res[form + "_ms"] = round(ms, 3)
+            res[form + "_gpx_s"] = round(px / ms / 1e6, 3)
+            res[form + "_same_output"] = bool(same)
+            res[form + "_speedup_vs_plain"] = round(res["plain_ms"] / ms, 3)
+            del keep
+        out[name] = res
+
+    compare("seeds16384", [c3], tune=True)
+    del c1, c2, c2b, c3
+    compare("batch256", synth.mixed_batch(256, workload_id=4), tune=True)
+    compare("batch512", synth.mixed_batch(512, workload_id=5), tune=True)
+    out["seconds"] = round(time.time() - t_start, 1)
+    return out
+
 
 
 def run_reference(args, rank: int, world: int):
@@ -320,6 +444,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tissue4096", choices=["tissue4096", "noiseblur512", "seeds16384"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--quick", action="store_true", help="skip the batched / learned comparisons")
+    ap.add_argument("--form-reps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

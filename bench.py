@@ -388,7 +388,7 @@ def run_forms(args, dev):
         plan = iwpp.iwpp_default_plan()
         if tune:
             Bt = iwpp.Batch(items, plan)
-            plan, tms = Bt.autotune(reps=1)
+            plan, tms = Bt.autotune(reps=2)
             res["autotuned_plan"] = plan.as_dict()
             del Bt
         for form, lsch in (("batched_static", False), ("batched_learned", True)):

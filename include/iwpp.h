@@ -218,7 +218,8 @@ IWPP_API int iwpp_graph_destroy(iwpp_graph graph);
 /*
  * Autotuner: picks the tile shape, sweep count and shared queue capacity of
  * *plan_inout by timing candidate plans on the batch itself (coordinate descent
- * from the given plan; best of `reps` runs each; CUDA events on `stream`). The
+ * from the given plan; best of `reps` runs each, each after writing a buffer of
+ * twice the L2 size; CUDA events on `stream`). The
  * markers are backed up first and restored after every trial and at the end, so
  * the batch's images are unchanged on return. This call allocates device memory
  * (backups, a workspace) and synchronises `stream`. cache_path (may be NULL) is a

@@ -308,12 +308,21 @@ int64_t batch_tiles(const iwpp_image *imgs, int n, const iwpp_plan &p, std::vect
     return (int64_t)total;
 }
 
+// Kernel variant of a batch: the specialised one when every image has the same pixel
+// type and connectivity, else the mixed one.
+static int batch_variant(const iwpp_image *imgs, int n) {
+    const int v = kind_of(imgs[0].dtype, imgs[0].connectivity);
+    for (int i = 1; i < n; i++)
+        if (kind_of(imgs[i].dtype, imgs[i].connectivity) != v) return kMixed;
+    return v;
+}
+
 static bool make_batch_layout(const iwpp_image *imgs, int n, const iwpp_plan &p, BatchLayout &L,
                               std::vector<uint32_t> *bases) {
     const int64_t nt = batch_tiles(imgs, n, p, bases);
     if (nt < 1) return false;
     L.ntiles = (uint32_t)nt;
-    L.grid = drain_grid(p, kMixed, L.ntiles);
+    L.grid = drain_grid(p, batch_variant(imgs, n), L.ntiles);
     if (L.grid <= 0) return false;
     L.ovcap = (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap);
     L.table = 256;
@@ -362,9 +371,10 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     a.defer_push = 1;
 
     const int shape = shape_index(p.tile_h, p.tile_w);
-    const KernelSet &k = kernels(shape, kMixed);
+    const int variant = batch_variant(imgs, n);
+    const KernelSet &k = kernels(shape, variant);
     const size_t smem = k.smem(a.qcap);
-    if (ensure_smem_attr(shape, kMixed, smem) != cudaSuccess) return IWPP_ERR_CUDA;
+    if (ensure_smem_attr(shape, variant, smem) != cudaSuccess) return IWPP_ERR_CUDA;
 
     // image table: descriptors travel as kernel parameters (no host-to-device copy)
     for (int first = 0; first < n; first += kDescChunk) {

@@ -212,7 +212,7 @@ struct Tile {
     static constexpr int EPC = 16 / S;                    // elements per 16-byte chunk
     static constexpr int ICH = TW / EPC + 1;              // chunks covering TW elements at any alignment
     static constexpr int NITEMS = PH * ICH;               // chunk slots of one loaded array
-    static constexpr size_t STAGE_BYTES = (size_t)2 * NITEMS * 16;
+    static constexpr size_t STAGE_BYTES = (size_t)(sizeof(T) == 2 ? 1 : 2) * NITEMS * 16;   // queue-area staging
     static constexpr int NDIR = CONN;
     static constexpr uint32_t QBIT = 1u;
     static_assert(NP < 65536, "queue entries are 16-bit padded indices");
@@ -223,7 +223,7 @@ struct Tile {
         uint32_t *halo0;    // NHALO: halo values when they were loaded
         uint32_t *misc;     // 32 flags
         uint16_t *q;        // 2 * qcap: wave queues ...
-        uint8_t *stage;     // ... whose space doubles as the staging area of a tile load
+        uint8_t *stage;     // ... whose space doubles as the marker staging area of a tile load
     };
     enum { M_NOTIFY = 0 /* 0..8 */, M_PRECOND = 9 };
 
@@ -286,45 +286,15 @@ struct Tile {
 
     // ---- HBM -> shared memory (all 32 lanes of the warp) ---------------------------------
     // Loads tile (ty, tx) with its one-pixel halo. Every full 16-byte chunk that covers the
-    // tile's own columns of a padded row is copied into the staging area with cp.async (all
-    // in flight at once, through L2 only so that J written by other warps is seen), then
-    // widened; the two halo columns are read element by element. Positions outside the image
-    // get J = flag only (value 0) and I = 0, so they can never be raised or queued. Halo
-    // words carry the queued flag; halo0 keeps the halo values.
-    static __device__ void load_tile(const ImageView &im, const Smem &s, int ty, int tx, int lane) {
-        const int y0 = ty * TH, x0 = tx * TW;
-        const size_t total = (size_t)im.H * (size_t)im.W;
-        const int xe = min(im.W, x0 + TW);             // end of the tile's own columns
-        uint8_t *stJ = s.stage, *stI = s.stage + NITEMS * 16;
-        // fill everything that may stick out of the image first
-        if (y0 == 0 || x0 == 0 || y0 + TH >= im.H || x0 + TW >= im.W) {
-            for (int p = lane; p < NP; p += 32) { s.J[p] = QBIT; s.I[p] = 0; }
-            __syncwarp();
-        }
-        for (int it = lane; it < NITEMS; it += 32) {
-            const int r = it / ICH, k = it % ICH;
-            const int gy = y0 + r - 1;
-            if (gy < 0 || gy >= im.H) continue;
-            const size_t rowbase = (size_t)gy * im.W;
-            const size_t chunk = (rowbase + x0) / EPC + k;
-            if (chunk * EPC >= rowbase + xe || (chunk + 1) * EPC > total) continue;
-            cp_async16(stJ + it * 16, reinterpret_cast<const uint4 *>(im.J) + chunk);
-            cp_async16(stI + it * 16, reinterpret_cast<const uint4 *>(im.I) + chunk);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        // the two halo columns, element by element, while the copies are in flight
-        for (int i = lane; i < 2 * PH; i += 32) {
-            const int r = i >> 1, c = (i & 1) ? TW : -1;
-            const int gy = y0 + r - 1, gx = x0 + c;
-            if (gy < 0 || gy >= im.H || gx < 0 || gx >= im.W) continue;
-            const size_t e = (size_t)gy * im.W + gx;
-            const uint32_t jv = to_dom(__ldcg(reinterpret_cast<const T *>(im.J) + e), im.flip);
-            const uint32_t iv = to_dom(reinterpret_cast<const T *>(im.I)[e], im.flip);
-            s.J[pidx(r, c)] = (jv << 1) | QBIT;
-            s.I[pidx(r, c)] = (uint16_t)iv;
-        }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        __syncwarp();
+    // tile's own columns of a padded row is copied with cp.async (all in flight at once,
+    // through L2 only, so that J written by other warps is seen): the mask bytes into the
+    // space of the J array (not yet in use), the marker bytes into the queue area. The mask
+    // is widened first, which frees the J array for the marker. The two halo columns are
+    // read element by element. Positions outside the image get J = flag only (value 0) and
+    // I = 0, so they can never be raised or queued. Halo words carry the queued flag.
+    template <bool IS_I>
+    static __device__ __forceinline__ void widen(const ImageView &im, const Smem &s, const uint8_t *stage, int y0,
+                                                 int x0, int xe, size_t total, int lane) {
         for (int it = lane; it < NITEMS; it += 32) {
             const int r = it / ICH, k = it % ICH;
             const int gy = y0 + r - 1;
@@ -334,7 +304,48 @@ struct Tile {
             const size_t chunk = lo / EPC + k;
             const size_t e0 = chunk * EPC;
             if (e0 >= hi) continue;
+            union { uint4 u; T e[EPC]; } v;
+            if (e0 + EPC <= total) {
+                v.u = *reinterpret_cast<const uint4 *>(stage + it * 16);
+            } else {
+#pragma unroll
+                for (int j = 0; j < EPC; j++)
+                    if (e0 + j < total)
+                        v.e[j] = IS_I ? reinterpret_cast<const T *>(im.I)[e0 + j]
+                                      : __ldcg(reinterpret_cast<const T *>(im.J) + e0 + j);
+            }
+            const int shift = pidx(r, 0) - x0;                         // + image column = padded index
+            const int base = (int)((int64_t)e0 - (int64_t)rowbase);    // image column of element 0
             const uint32_t hflag = (r == 0 || r == PH - 1) ? QBIT : 0u;
+            const bool full = e0 >= lo && e0 + EPC <= hi;
+#pragma unroll
+            for (int j = 0; j < EPC; j++) {
+                if (!full && (e0 + j < lo || e0 + j >= hi)) continue;
+                const uint32_t x = to_dom(v.e[j], im.flip);
+                if (IS_I) s.I[shift + base + j] = (uint16_t)x;
+                else s.J[shift + base + j] = (x << 1) | hflag;
+            }
+        }
+    }
+
+    // u8 tiles stage both arrays in the queue area and widen them in one pass; u16 tiles,
+    // whose staging is twice as large, stage the mask inside the J array (free until the
+    // mask is widened), so that a u16 tile needs no more shared memory than a u8 one.
+    static constexpr bool SPLIT = sizeof(T) == 2;
+
+    // Both arrays from their staging areas in one pass over the chunks.
+    static __device__ __forceinline__ void widen_both(const ImageView &im, const Smem &s, const uint8_t *stJ,
+                                                      const uint8_t *stI, int y0, int x0, int xe, size_t total,
+                                                      int lane) {
+        for (int it = lane; it < NITEMS; it += 32) {
+            const int r = it / ICH, k = it % ICH;
+            const int gy = y0 + r - 1;
+            if (gy < 0 || gy >= im.H) continue;
+            const size_t rowbase = (size_t)gy * im.W;
+            const size_t lo = rowbase + x0, hi = rowbase + xe;
+            const size_t chunk = lo / EPC + k;
+            const size_t e0 = chunk * EPC;
+            if (e0 >= hi) continue;
             union { uint4 u; T e[EPC]; } vj, vi;
             if (e0 + EPC <= total) {
                 vj.u = *reinterpret_cast<const uint4 *>(stJ + it * 16);
@@ -348,25 +359,99 @@ struct Tile {
                     }
                 }
             }
-            uint32_t *jrow = s.J + pidx(r, 0) - (int)(lo - rowbase);   // jrow[x - rowbase... ] see below
-            uint16_t *irow = s.I + pidx(r, 0) - (int)(lo - rowbase);
-            // element e of the image row sits at column (e - lo) of the tile
-            const int base = (int)((int64_t)e0 - (int64_t)rowbase);    // image column of element 0
+            const int shift = pidx(r, 0) - x0;
+            const int base = (int)((int64_t)e0 - (int64_t)rowbase);
+            const uint32_t hflag = (r == 0 || r == PH - 1) ? QBIT : 0u;
             if (e0 >= lo && e0 + EPC <= hi) {
 #pragma unroll
                 for (int j = 0; j < EPC; j++) {
-                    jrow[base + j] = (to_dom(vj.e[j], im.flip) << 1) | hflag;
-                    irow[base + j] = (uint16_t)to_dom(vi.e[j], im.flip);
+                    s.J[shift + base + j] = (to_dom(vj.e[j], im.flip) << 1) | hflag;
+                    s.I[shift + base + j] = (uint16_t)to_dom(vi.e[j], im.flip);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < EPC; j++) {
                     const size_t e = e0 + j;
                     if (e < lo || e >= hi) continue;
-                    jrow[base + j] = (to_dom(vj.e[j], im.flip) << 1) | hflag;
-                    irow[base + j] = (uint16_t)to_dom(vi.e[j], im.flip);
+                    s.J[shift + base + j] = (to_dom(vj.e[j], im.flip) << 1) | hflag;
+                    s.I[shift + base + j] = (uint16_t)to_dom(vi.e[j], im.flip);
                 }
             }
+        }
+    }
+
+    static __device__ void load_tile(const ImageView &im, const Smem &s, int ty, int tx, int lane) {
+        static_assert((size_t)NITEMS * 16 <= (size_t)NP * 4, "mask staging must fit in the J array");
+        const int y0 = ty * TH, x0 = tx * TW;
+        const size_t total = (size_t)im.H * (size_t)im.W;
+        const int xe = min(im.W, x0 + TW);             // end of the tile's own columns
+        uint8_t *stJ = s.stage;
+        uint8_t *stI = SPLIT ? reinterpret_cast<uint8_t *>(s.J) : s.stage + NITEMS * 16;
+        const bool edge = y0 == 0 || x0 == 0 || y0 + TH >= im.H || x0 + TW >= im.W;
+        if (edge) {
+            for (int p = lane; p < NP; p += 32) {
+                s.I[p] = 0;
+                if (!SPLIT) s.J[p] = QBIT;
+            }
+            if (!SPLIT) __syncwarp();
+        }
+        for (int it = lane; it < NITEMS; it += 32) {
+            const int r = it / ICH, k = it % ICH;
+            const int gy = y0 + r - 1;
+            if (gy < 0 || gy >= im.H) continue;
+            const size_t rowbase = (size_t)gy * im.W;
+            const size_t chunk = (rowbase + x0) / EPC + k;
+            if (chunk * EPC >= rowbase + xe || (chunk + 1) * EPC > total) continue;
+            cp_async16(stJ + it * 16, reinterpret_cast<const uint4 *>(im.J) + chunk);
+            cp_async16(stI + it * 16, reinterpret_cast<const uint4 *>(im.I) + chunk);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        if (!SPLIT) {
+            // the two halo columns, element by element, while the copies are in flight
+            for (int i = lane; i < 2 * PH; i += 32) {
+                const int r = i >> 1, c = (i & 1) ? TW : -1;
+                const int gy = y0 + r - 1, gx = x0 + c;
+                if (gy < 0 || gy >= im.H || gx < 0 || gx >= im.W) continue;
+                const size_t e = (size_t)gy * im.W + gx;
+                s.J[pidx(r, c)] = (to_dom(__ldcg(reinterpret_cast<const T *>(im.J) + e), im.flip) << 1) | QBIT;
+                s.I[pidx(r, c)] = (uint16_t)to_dom(reinterpret_cast<const T *>(im.I)[e], im.flip);
+            }
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            __syncwarp();
+            widen_both(im, s, stJ, stI, y0, x0, xe, total, lane);
+            __syncwarp();
+            return;
+        }
+        constexpr int HC = (2 * PH + 31) / 32;
+        uint32_t hj[HC], hi_[HC];
+#pragma unroll
+        for (int q = 0; q < HC; q++) {
+            const int i = lane + 32 * q;
+            hj[q] = QBIT;
+            hi_[q] = 0;
+            const int r = i >> 1, c = (i & 1) ? TW : -1;
+            const int gy = y0 + r - 1, gx = x0 + c;
+            if (i >= 2 * PH || gy < 0 || gy >= im.H || gx < 0 || gx >= im.W) continue;
+            const size_t e = (size_t)gy * im.W + gx;
+            hj[q] = (to_dom(__ldcg(reinterpret_cast<const T *>(im.J) + e), im.flip) << 1) | QBIT;
+            hi_[q] = to_dom(reinterpret_cast<const T *>(im.I)[e], im.flip);
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncwarp();
+        widen<true>(im, s, stI, y0, x0, xe, total, lane);
+        __syncwarp();   // the mask bytes in the J array are consumed
+        if (edge) {
+            for (int p = lane; p < NP; p += 32) s.J[p] = QBIT;
+            __syncwarp();
+        }
+        widen<false>(im, s, stJ, y0, x0, xe, total, lane);
+#pragma unroll
+        for (int q = 0; q < HC; q++) {
+            const int i = lane + 32 * q;
+            if (i >= 2 * PH) continue;
+            const int r = i >> 1, c = (i & 1) ? TW : -1;
+            s.J[pidx(r, c)] = hj[q];
+            s.I[pidx(r, c)] = (uint16_t)hi_[q];
         }
         __syncwarp();
     }
@@ -871,7 +956,7 @@ __device__ inline void flush_stats(const EngineArgs &a, const VisitStats &st, un
     }
 }
 
-// ---- kernels: one image of one pixel type and connectivity ---------------------------------------
+// ---- kernels: images of one pixel type and connectivity (one image, or a uniform batch) -----------
 template <typename T, int CONN, int TH, int TW>
 __global__ void __launch_bounds__(kThreads) scan_kernel(EngineArgs a) {
     using TL = Tile<T, CONN, TH, TW>;
@@ -880,7 +965,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(EngineArgs a) {
     uint8_t *wsmem = smem_raw + warp * TL::smem_per_warp(a.qcap);
     const uint32_t nworkers = gridDim.x * kWarpsPerCta;
     for (uint32_t t = blockIdx.x * kWarpsPerCta + warp; t < a.ntiles; t += nworkers)
-        scan_tile<T, CONN, TH, TW>(a, a.img0, t, wsmem, lane);
+        scan_tile<T, CONN, TH, TW>(a, image_of(a, t), t, wsmem, lane);
 }
 
 template <typename T, int CONN, int TH, int TW>
@@ -897,7 +982,7 @@ __global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_kernel(Engine
         const uint32_t t = acquire_tile(a, first, idle, lane);
         if (t == kDone) break;
         const unsigned long long b0 = globaltimer_ns();
-        visit_tile<T, CONN, TH, TW>(a, a.img0, t, first, wsmem, ovf, st, lane);
+        visit_tile<T, CONN, TH, TW>(a, image_of(a, t), t, first, wsmem, ovf, st, lane);
         busy += globaltimer_ns() - b0;
     }
     flush_stats(a, st, idle, busy, lane);

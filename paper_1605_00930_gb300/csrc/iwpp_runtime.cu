@@ -63,9 +63,16 @@ struct Tuner {
     std::vector<size_t> bytes;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    void *flush = nullptr;      // written before every trial so that no trial starts with a warm L2
+    size_t flush_bytes = 0;
     int reps;
 
     int init() {
+        int dev = 0, l2 = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        flush_bytes = (size_t)(l2 > 0 ? l2 : (64 << 20)) * 2;
+        if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) return IWPP_ERR_CUDA;
         backup.assign(n, nullptr);
         bytes.assign(n, 0);
         for (int i = 0; i < n; i++) {
@@ -100,6 +107,7 @@ struct Tuner {
         float best = -1.f;
         for (int r = 0; r < reps; r++) {
             if (restore() != IWPP_OK) break;
+            if (cudaMemsetAsync(flush, r & 0xFF, flush_bytes, stream) != cudaSuccess) break;
             cudaEventRecord(e0, stream);
             if (reconstruct_batch(imgs, n, &p, nullptr, nullptr, nullptr, ws, ws_bytes, stream) != IWPP_OK) break;
             cudaEventRecord(e1, stream);
@@ -119,6 +127,7 @@ struct Tuner {
         for (void *b : backup)
             if (b) cudaFree(b);
         if (ws) cudaFree(ws);
+        if (flush) cudaFree(flush);
     }
 };
 

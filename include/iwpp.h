@@ -304,6 +304,35 @@ IWPP_API int iwpp_tile_work_to_blocks(const iwpp_image *imgs, int n, const iwpp_
                                       void *sched_ws, size_t sws_bytes, void *stream);
 
 /*
+ * ---- Reconstruction without any allocation ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory where they reconstruct: code running under a memory budget
+ * fixed at start-up, plug-ins whose host framework owns every allocation, or real-time
+ * loops where cudaMalloc (which may synchronise the device) is not allowed.
+ *
+ * iwpp_reconstruct_noalloc is iwpp_reconstruct with the default plan, except that its
+ * workspace is a device array of IWPP_NOALLOC_SCRATCH_BYTES (8 MiB) inside the library,
+ * held by every GPU that loads the library until the process exits. It calls no
+ * cudaMalloc, cudaFree or other allocating routine. The caller passes the marker
+ * (overwritten by the result) and the mask, as for iwpp_reconstruct.
+ *   - Images whose workspace would exceed the array are rejected with
+ *     IWPP_ERR_WORKSPACE before anything is enqueued (about 400 megapixels on a GB300;
+ *     iwpp_workspace_bytes(H, W, dtype, NULL) gives the need).
+ *   - The first call on a device looks up the array's device address for that device
+ *     (with that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one array; each call resets the parts that must
+ *     start at zero. Calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on it and must be serialised by the caller.
+ *   - status_out (may be NULL): when given, the call waits for `stream` and stores the
+ *     device status (IWPP_OK or an iwpp_status code) there; otherwise the call is
+ *     asynchronous and the device status is not reported.
+ * Returns IWPP_OK or a host-detected error code.
+ */
+#define IWPP_NOALLOC_SCRATCH_BYTES (8u << 20)
+IWPP_API int iwpp_reconstruct_noalloc(void *marker_inout, const void *mask, int64_t H, int64_t W,
+                                      int connectivity, int op, int dtype, void *stream, int *status_out);
+
+/*
  * Work counters of the last call (single image or batch) that used `workspace`: tile
  * visits by the persistent kernel, wave-queue entries processed (pops),
  * entries created by the visits' initial scans (seeds), wave steps run, and

@@ -103,6 +103,9 @@ _PROTOS = [
     ("iwpp_tile_work_to_blocks", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                 ctypes.c_void_p]),
+    ("iwpp_reconstruct_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.POINTER(ctypes.c_int)]),
     ("iwpp_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("iwpp_work_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -266,6 +269,12 @@ def iwpp_schedule_learned(imgs, plan, params, order, sweeps, sws, stream=None):
 def iwpp_tile_work_to_blocks(imgs, plan, tile_work, block_work, sws, stream=None):
     _check(lib().iwpp_tile_work_to_blocks(imgs, len(imgs), _pp(plan), _ptr(tile_work), _ptr(block_work),
                                           _ptr(sws), sws.numel(), _stream_handle(stream)), "iwpp_tile_work_to_blocks")
+
+
+def iwpp_reconstruct_noalloc(marker_ptr, mask_ptr, H, W, conn, op, dtype, stream, status=None) -> int:
+    """C call without a caller workspace; `status` (a ctypes.c_int) receives the device status."""
+    return lib().iwpp_reconstruct_noalloc(marker_ptr, mask_ptr, H, W, conn, op, dtype, stream,
+                                          ctypes.byref(status) if status is not None else None)
 
 
 def iwpp_sync_status(ws_ptr, stream) -> int:

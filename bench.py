@@ -387,6 +387,8 @@ def run_forms(args, dev):
         res["plain_gpx_s"] = round(px / ms / 1e6, 3)
         plan = iwpp.iwpp_default_plan()
         if tune:
+            for (m, _, _, _), m0 in zip(items, init):   # tune on the inputs, not on the result
+                m.copy_(m0)
             Bt = iwpp.Batch(items, plan)
             plan, tms = Bt.autotune(reps=2)
             res["autotuned_plan"] = plan.as_dict()

@@ -68,7 +68,7 @@ typedef enum {
  * Execution plan: the knobs of the propagation engine. None of them can change
  * the result (the reconstruction is unique); they change only the work done.
  *   tile_h, tile_w     tile shape, one warp per tile; must be one of the
- *                      compiled shapes (32x32, 32x64, 64x64 — see
+ *                      compiled shapes (32x32, 32x64, 64x64, 16x32, 16x64 — see
  *                      iwpp_tile_shape_supported)
  *   sweeps             raster + anti-raster sweep pairs run over every tile
  *                      before the queue phase (Algorithm 7's scanning phase,
@@ -80,6 +80,14 @@ typedef enum {
  *                      warp's global overflow queue (16 .. tile_h * tile_w)
  *   blocks_per_sm      persistent-kernel CTAs (of 4 warps) per SM
  *                      (0 = occupancy maximum)
+ *   local_solver       how the persistent kernel settles a tile it visits:
+ *                      IWPP_SOLVER_QUEUE, the FIFO wave queues of Algorithm
+ *                      7's queue phase in shared memory, or
+ *                      IWPP_SOLVER_REGISTER, the tile held in registers (two
+ *                      columns per lane) and swept down and up until no pixel
+ *                      changes (Algorithm 1's update in Gauss-Seidel order);
+ *                      the register solver needs tile_w == 64, tile_h <= 16
+ *   reserved           must be 0
  *   watchdog_ns        the persistent kernel gives up with IWPP_ERR_TIMEOUT
  *                      when a wait for work lasts longer than this
  *                      (0 = default, 10 s)
@@ -90,8 +98,13 @@ typedef struct {
     int32_t revisit_sweeps;
     int32_t smem_queue_cap;
     int32_t blocks_per_sm;
+    int32_t local_solver;
+    int32_t reserved;
     int64_t watchdog_ns;
 } iwpp_plan;
+
+/* Values of iwpp_plan.local_solver. */
+enum { IWPP_SOLVER_QUEUE = 0, IWPP_SOLVER_REGISTER = 1 };
 
 /* Fills *plan with the static default schedule. Returns IWPP_OK. */
 IWPP_API int iwpp_default_plan(iwpp_plan *plan);
@@ -216,8 +229,9 @@ IWPP_API int iwpp_graph_launch(iwpp_graph graph, void *stream);
 IWPP_API int iwpp_graph_destroy(iwpp_graph graph);
 
 /*
- * Autotuner: picks the tile shape, sweep count and shared queue capacity of
- * *plan_inout by timing candidate plans on the batch itself (coordinate descent
+ * Autotuner: picks the local solver with its tile shape, the sweep count and
+ * (queue solver) the shared queue capacity of *plan_inout by timing candidate
+ * plans on the batch itself (coordinate descent
  * from the given plan; best of `reps` runs each, each after writing a buffer of
  * twice the L2 size; CUDA events on `stream`). The
  * markers are backed up first and restored after every trial and at the end, so

@@ -21,6 +21,7 @@
 
 #include "../../include/iwpp.h"
 #include "iwpp_engine.cuh"
+#include "iwpp_regtile.cuh"
 #include "iwpp_host.h"
 
 namespace iwpp {
@@ -29,7 +30,7 @@ namespace iwpp {
 struct ShapeInfo {
     int th, tw;
 };
-static const ShapeInfo kShapes[] = {{32, 32}, {32, 64}, {64, 64}};
+static const ShapeInfo kShapes[] = {{32, 32}, {32, 64}, {64, 64}, {16, 32}, {16, 64}};
 static constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 int shape_index(int th, int tw) {
@@ -44,6 +45,8 @@ struct KernelSet {
     void (*scan)(EngineArgs);
     void (*drain)(EngineArgs);
     size_t (*smem)(uint32_t);
+    void (*drain_reg)(EngineArgs);   // register-resident local solver (32-wide tiles), else null
+    size_t (*smem_reg)(uint32_t);
 };
 static constexpr int kMixed = 4;
 
@@ -53,6 +56,13 @@ static KernelSet make_set() {
     k.scan = scan_kernel<T, CONN, TH, TW>;
     k.drain = drain_kernel<T, CONN, TH, TW>;
     k.smem = &Tile<T, CONN, TH, TW>::smem_bytes;
+    if constexpr (TW == 64 && TH <= 16) {
+        k.drain_reg = drain_reg_kernel<T, CONN, TH>;
+        k.smem_reg = &RegTile<T, CONN, TH>::smem_bytes;
+    } else {
+        k.drain_reg = nullptr;
+        k.smem_reg = nullptr;
+    }
     return k;
 }
 
@@ -70,6 +80,13 @@ static void fill_shape(KernelSet (&row)[5]) {
     row[kMixed].scan = scan_mixed_kernel<TH, TW>;
     row[kMixed].drain = drain_mixed_kernel<TH, TW>;
     row[kMixed].smem = &mixed_smem_bytes<TH, TW>;
+    if constexpr (TW == 64 && TH <= 16) {
+        row[kMixed].drain_reg = drain_reg_mixed_kernel<TH>;
+        row[kMixed].smem_reg = &RegTile<uint16_t, 8, TH>::smem_bytes;
+    } else {
+        row[kMixed].drain_reg = nullptr;
+        row[kMixed].smem_reg = nullptr;
+    }
 }
 
 static KernelSet g_sets[kNumShapes][5];
@@ -81,6 +98,8 @@ static void init_sets() {
     fill_shape<32, 32>(g_sets[0]);
     fill_shape<32, 64>(g_sets[1]);
     fill_shape<64, 64>(g_sets[2]);
+    fill_shape<16, 32>(g_sets[3]);
+    fill_shape<16, 64>(g_sets[4]);
 }
 
 static int kind_of(int dtype, int conn) { return (dtype == IWPP_U16 ? 1 : 0) | (conn == 8 ? 2 : 0); }
@@ -102,6 +121,10 @@ static cudaError_t ensure_smem_attr(int shape, int v, size_t bytes) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute((const void *)k.drain, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     if (e != cudaSuccess) return e;
+    if (k.drain_reg) {
+        e = cudaFuncSetAttribute((const void *)k.drain_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e != cudaSuccess) return e;
+    }
     done = want;
     return cudaSuccess;
 }
@@ -115,16 +138,25 @@ int device_sm_count() {
     return n;
 }
 
+// The persistent kernel of a plan (queue or register local solver) and its shared memory.
+static void (*drain_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
+    return p.local_solver == IWPP_SOLVER_REGISTER ? k.drain_reg : k.drain;
+}
+static size_t drain_smem(const iwpp_plan &p, const KernelSet &k) {
+    return p.local_solver == IWPP_SOLVER_REGISTER ? k.smem_reg((uint32_t)p.smem_queue_cap)
+                                                  : k.smem((uint32_t)p.smem_queue_cap);
+}
+
 // Persistent CTAs for a plan: blocks_per_sm (or the occupancy maximum) x SMs, never more
 // CTAs than needed to give every tile its own warp.
 static int drain_grid(const iwpp_plan &p, int v, uint32_t ntiles) {
     const int shape = shape_index(p.tile_h, p.tile_w);
     const KernelSet &k = kernels(shape, v);
-    const size_t smem = k.smem((uint32_t)p.smem_queue_cap);
-    if (ensure_smem_attr(shape, v, smem) != cudaSuccess) return 0;
+    const size_t smem = drain_smem(p, k);
+    if (ensure_smem_attr(shape, v, k.smem((uint32_t)p.smem_queue_cap)) != cudaSuccess) return 0;
     int bps = p.blocks_per_sm;
     if (bps <= 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k.drain, kThreads, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, drain_fn(p, k), kThreads, smem) != cudaSuccess)
             return 0;
         if (bps <= 0) return 0;
     }
@@ -142,16 +174,22 @@ bool plan_valid(const iwpp_plan &p) {
     if (p.smem_queue_cap < 16 || p.smem_queue_cap > p.tile_h * p.tile_w) return false;
     if (p.blocks_per_sm < 0 || p.blocks_per_sm > 32) return false;
     if (p.watchdog_ns < 0) return false;
+    if (p.local_solver != IWPP_SOLVER_QUEUE && p.local_solver != IWPP_SOLVER_REGISTER) return false;
+    if (p.local_solver == IWPP_SOLVER_REGISTER && (p.tile_w != 64 || p.tile_h > 16)) return false;
+    if (p.reserved != 0) return false;
     return true;
 }
 
+// The measured best static plan: 16 x 64 tiles settled by the register solver.
 void default_plan(iwpp_plan *p) {
-    p->tile_h = 32;
-    p->tile_w = 32;
+    p->tile_h = 16;
+    p->tile_w = 64;
     p->sweeps = 1;
     p->revisit_sweeps = 0;
     p->smem_queue_cap = 512;
     p->blocks_per_sm = 0;
+    p->local_solver = IWPP_SOLVER_REGISTER;
+    p->reserved = 0;
     p->watchdog_ns = 0;
 }
 
@@ -258,7 +296,7 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
         const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
         k.scan<<<scan_grid, kThreads, smem, stream>>>(a);
     }
-    if (phases & kPhaseDrain) k.drain<<<L.grid, kThreads, smem, stream>>>(a);
+    if (phases & kPhaseDrain) drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
 }
 
@@ -397,7 +435,7 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     const uint32_t cgrid = (L.ntiles + 255) / 256 < (uint32_t)(sms * 8) ? (L.ntiles + 255) / 256 : (uint32_t)(sms * 8);
     compact_kernel<<<cgrid, 256, 0, stream>>>(a);
     finalize_queue_kernel<<<cgrid, 256, 0, stream>>>(a);
-    k.drain<<<L.grid, kThreads, smem, stream>>>(a);
+    drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
 }
 

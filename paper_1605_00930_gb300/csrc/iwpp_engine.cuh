@@ -846,6 +846,27 @@ struct VisitStats {
     unsigned long long visits, pops, seeds, waves;
 };
 
+// End of a visit round (whole warp, after the tile's stores and notifications are
+// fenced): ACTIVE -> IDLE and one fewer pending tile, unless the tile was notified while
+// this warp held it; then it stays ACTIVE and the warp processes it again (returns true).
+__device__ inline bool finish_tile(const EngineArgs &a, uint32_t t, int lane) {
+    uint32_t redo = 0;
+    if (lane == 0) {
+        const uint32_t busy_st = ST_ACTIVE | ST_VISITED;
+        const uint32_t r = atomicCAS(a.state + t, busy_st, ST_VISITED);
+        if (r == busy_st) {
+            __threadfence();
+            atomicSub(&a.hdr->pending, 1u);
+        } else {
+            atomicAnd(a.state + t, ~ST_PENDING);   // notified while ACTIVE: go again
+            redo = 1;
+        }
+        __threadfence();
+        redo = redo && !fatal(a.hdr);
+    }
+    return __shfl_sync(0xffffffffu, redo, 0) != 0;
+}
+
 // One visit of tile t by the persistent kernel, including the re-processing rounds when
 // the tile is notified while this warp holds it. Lane 0 has already moved the tile to
 // ACTIVE; on return it is IDLE (or the run is stopping on an error).
@@ -885,22 +906,7 @@ __device__ void visit_tile(const EngineArgs &a, const ImageView &im, uint32_t t,
         __threadfence();
         __syncwarp();
         TL::send_notifications(s, a, im, ty, tx, lane);
-        uint32_t redo = 0;
-        if (lane == 0) {
-            const uint32_t busy_st = ST_ACTIVE | ST_VISITED;
-            const uint32_t r = atomicCAS(a.state + t, busy_st, ST_VISITED);
-            if (r == busy_st) {
-                __threadfence();
-                atomicSub(&a.hdr->pending, 1u);
-            } else {
-                atomicAnd(a.state + t, ~ST_PENDING);   // notified while ACTIVE: go again
-                redo = 1;
-            }
-            __threadfence();
-            redo = redo && !fatal(a.hdr);
-        }
-        redo = __shfl_sync(0xffffffffu, redo, 0);
-        if (!redo) break;
+        if (!finish_tile(a, t, lane)) break;
         // Re-process: the interior in shared memory is what this warp stored; only the
         // halo can have changed since.
         TL::clear_flags(s, lane);

@@ -1,0 +1,416 @@
+// iwpp_regtile.cuh — register-resident local solver for 64-wide tiles (sm_103a).
+//
+// Alternative to the shared-memory wave queues of iwpp_engine.cuh for the persistent
+// kernel's tile visits. The tile (TH rows x 64 columns) lives in registers: lane c holds
+// columns 2c (low 16 bits) and 2c + 1 (high 16 bits) of every row, one register per row
+// for J and one for I, in the dilation domain; both columns are updated at once with the
+// packed min.u16x2 / max.u16x2 instructions. The visit repeats Gauss-Seidel passes of the
+// update of Algorithm 1 (Eq. "recon") until a pass pair changes nothing or a residual
+// check finds no pixel that can still rise:
+//   down pass, rows top to bottom:  J(p) <- min(I(p), max(J(p), W, E, N, and NW, NE for 8-conn)),
+//                                   N / NW / NE already updated in this pass;
+//   up pass, rows bottom to top:    the same with S, SW, SE.
+// Horizontal neighbours come from the adjacent half of the register or, across lanes, from
+// one warp shuffle per direction and row; the halo columns come from shared memory. There
+// are no shared-memory atomics and no queues. At convergence every pixel satisfies
+// J = min(I, max over its neighbourhood) for the current halo: the same local fixed point
+// the queue solver reaches, so the global result is the same (the reconstruction is unique).
+#pragma once
+#include "iwpp_engine.cuh"
+
+namespace iwpp {
+
+__device__ __forceinline__ uint32_t max2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t min2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// Left neighbours of a packed pair: (column 2c - 1, column 2c) from the previous lane's
+// pair `p` and this lane's pair `v`; right neighbours: (column 2c + 1, column 2c + 2).
+__device__ __forceinline__ uint32_t left_of(uint32_t p, uint32_t v) { return __byte_perm(p, v, 0x5432); }
+__device__ __forceinline__ uint32_t right_of(uint32_t v, uint32_t n) { return __byte_perm(v, n, 0x5432); }
+
+template <typename T, int CONN, int TH>
+struct RegTile {
+    static_assert(TH >= 2 && TH <= 30, "tile rows (one lane per halo row)");
+    static constexpr int TW = 64;
+    struct Smem {
+        uint32_t *hxJ;          // 2 x (TH + 2): [0..TH+1] left halo column << 16, [TH+2..] right halo column
+        uint32_t *hlI, *hrI;    // TH + 2: mask of the halo columns, index = row + 1
+        uint32_t *col0, *col63; // TH: the tile's first and last column after a solve
+        uint32_t *misc;         // 16: notification flags
+    };
+    static constexpr size_t kWords = 4 * (TH + 2) + 2 * TH + 16;
+    static __host__ __device__ size_t smem_per_warp(uint32_t) { return (kWords * 4 + 15) & ~(size_t)15; }
+    static size_t smem_bytes(uint32_t q) { return smem_per_warp(q) * kWarpsPerCta; }
+
+    static __device__ Smem carve(uint8_t *base) {
+        Smem s;
+        uint32_t *w = reinterpret_cast<uint32_t *>(base);
+        s.hxJ = w; w += 2 * (TH + 2);
+        s.hlI = w; w += TH + 2;
+        s.hrI = w; w += TH + 2;
+        s.col0 = w; w += TH;
+        s.col63 = w; w += TH;
+        s.misc = w;
+        return s;
+    }
+
+    static __device__ __forceinline__ uint32_t ld1(const uint8_t *p, size_t e, bool cg) {
+        const T *q = reinterpret_cast<const T *>(p) + e;
+        return (uint32_t)(cg ? __ldcg(q) : *q);
+    }
+
+    // Pixels (y, gx) and (y, gx + 1) of plane p, packed, flipped, 0 outside the image.
+    // Branch-free: both loads use clamped coordinates (always a valid address) and the
+    // out-of-image halves are zeroed afterwards, so a run of these calls issues all its
+    // loads before the first result is needed.
+    static __device__ __forceinline__ uint32_t ld_pair(const ImageView &im, const uint8_t *p, int y, int gx,
+                                                       bool cg) {
+        const bool yin = y >= 0 && y < im.H;
+        const size_t row = (size_t)min(max(y, 0), im.H - 1) * im.W;
+        const uint32_t a = ld1(p, row + min(gx, im.W - 1), cg), b = ld1(p, row + min(gx + 1, im.W - 1), cg);
+        return ((yin && gx < im.W) ? (a ^ im.flip) : 0u) | (((yin && gx + 1 < im.W) ? (b ^ im.flip) : 0u) << 16);
+    }
+
+    // Raw pair at element e (even; the row is 2-pixel aligned when W is even) and its
+    // packed form: one 16-bit (u8) or 32-bit (u16) load.
+    static __device__ __forceinline__ uint32_t ld_raw(const uint8_t *p, size_t e, bool cg) {
+        if (sizeof(T) == 1) {
+            const uint16_t *q = reinterpret_cast<const uint16_t *>(p + e);
+            return (uint32_t)(cg ? __ldcg(q) : *q);
+        }
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(p + 2 * e);
+        return cg ? __ldcg(q) : *q;
+    }
+    static __device__ __forceinline__ uint32_t unpack_raw(uint32_t w) {
+        return sizeof(T) == 1 ? __byte_perm(w, 0u, 0x4140) : w;
+    }
+
+    // Halo: top and bottom rows into registers (this lane's pair), the two halo columns
+    // (with corners) into shared memory. 0 outside the image.
+    static __device__ void load_halo(const ImageView &im, const Smem &s, int y0, int x0, uint32_t &jt,
+                                     uint32_t &jb, uint32_t &it, uint32_t &ib, bool withI, int lane) {
+        const int gx = x0 + 2 * lane;
+        jt = ld_pair(im, im.J, y0 - 1, gx, true);
+        jb = ld_pair(im, im.J, y0 + TH, gx, true);
+        if (withI) {
+            it = ld_pair(im, im.I, y0 - 1, gx, false);
+            ib = ld_pair(im, im.I, y0 + TH, gx, false);
+        }
+        if (lane < TH + 2) {
+            const int gy = y0 + lane - 1;
+            const bool rowin = gy >= 0 && gy < im.H;
+            const bool lin = rowin && x0 > 0, rin = rowin && x0 + TW < im.W;
+            const size_t row = (size_t)min(max(gy, 0), im.H - 1) * im.W;
+            const size_t el = row + max(x0 - 1, 0), er = row + min(x0 + TW, im.W - 1);
+            const uint32_t lj = ld1(im.J, el, true), rj = ld1(im.J, er, true);
+            uint32_t li = 0, ri = 0;
+            if (withI) {
+                li = ld1(im.I, el, false);
+                ri = ld1(im.I, er, false);
+            }
+            s.hxJ[lane] = lin ? (lj ^ im.flip) << 16 : 0u;
+            s.hxJ[TH + 2 + lane] = rin ? rj ^ im.flip : 0u;
+            if (withI) {
+                s.hlI[lane] = lin ? li ^ im.flip : 0u;
+                s.hrI[lane] = rin ? ri ^ im.flip : 0u;
+            }
+        }
+        __syncwarp();
+    }
+
+    static __device__ void load(const ImageView &im, const Smem &s, int y0, int x0, uint32_t (&J)[TH],
+                                uint32_t (&I)[TH], uint32_t &jt, uint32_t &jb, uint32_t &it, uint32_t &ib,
+                                int lane) {
+        const int gx = x0 + 2 * lane;
+        if ((im.W & 1) == 0 && x0 + TW <= im.W) {   // whole 64-column span inside, rows aligned
+            const uint32_t f2 = im.flip | (im.flip << 16);
+#pragma unroll
+            for (int r = 0; r < TH; r++) {
+                const size_t e = (size_t)min(y0 + r, im.H - 1) * im.W + gx;
+                J[r] = ld_raw(im.J, e, true);
+                I[r] = ld_raw(im.I, e, false);
+            }
+#pragma unroll
+            for (int r = 0; r < TH; r++) {
+                const bool in = y0 + r < im.H;
+                J[r] = in ? unpack_raw(J[r]) ^ f2 : 0u;
+                I[r] = in ? unpack_raw(I[r]) ^ f2 : 0u;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < TH; r++) {
+                J[r] = ld_pair(im, im.J, y0 + r, gx, true);
+                I[r] = ld_pair(im, im.I, y0 + r, gx, false);
+            }
+        }
+        load_halo(im, s, y0, x0, jt, jb, it, ib, true, lane);
+    }
+
+    // Horizontal max of a packed row over (left, self, right); `h` is this lane's halo word
+    // (lane 0: left halo column << 16, lane 31: right halo column, others unused).
+    static __device__ __forceinline__ uint32_t hmax(uint32_t v, uint32_t h, int lane) {
+        uint32_t p = __shfl_up_sync(0xffffffffu, v, 1), n = __shfl_down_sync(0xffffffffu, v, 1);
+        if (lane == 0) p = h;
+        if (lane == 31) n = h;
+        return max2(v, max2(left_of(p, v), right_of(v, n)));
+    }
+
+    // One down pass; returns this lane's mask of changed rows.
+    static __device__ __forceinline__ uint32_t pass_down(const uint32_t *hx, uint32_t (&J)[TH],
+                                                         const uint32_t (&I)[TH], uint32_t jt, int lane) {
+        uint32_t chg = 0, up = jt, hprev = hx[0];
+#pragma unroll
+        for (int r = 0; r < TH; r++) {
+            const uint32_t hcur = hx[r + 1], v = J[r];
+            uint32_t m = max2(hmax(v, hcur, lane), up);
+            if (CONN == 8) m = max2(m, hmax(up, hprev, lane));
+            const uint32_t nv = min2(I[r], m);
+            chg |= (uint32_t)(nv != v) << r;
+            J[r] = nv;
+            up = nv;
+            hprev = hcur;
+        }
+        return chg;
+    }
+
+    static __device__ __forceinline__ uint32_t pass_up(const uint32_t *hx, uint32_t (&J)[TH],
+                                                       const uint32_t (&I)[TH], uint32_t jb, int lane) {
+        uint32_t chg = 0, dn = jb, hnext = hx[TH + 1];
+#pragma unroll
+        for (int r = TH - 1; r >= 0; r--) {
+            const uint32_t hcur = hx[r + 1], v = J[r];
+            uint32_t m = max2(hmax(v, hcur, lane), dn);
+            if (CONN == 8) m = max2(m, hmax(dn, hnext, lane));
+            const uint32_t nv = min2(I[r], m);
+            chg |= (uint32_t)(nv != v) << r;
+            J[r] = nv;
+            dn = nv;
+            hnext = hcur;
+        }
+        return chg;
+    }
+
+    // Is some pixel of the tile still below min(I, max over its neighbourhood)? The rows
+    // are independent here, so this costs far less latency than another pass pair.
+    static __device__ __forceinline__ bool improvable(const uint32_t *hx, const uint32_t (&J)[TH],
+                                                      const uint32_t (&I)[TH], uint32_t jt, uint32_t jb,
+                                                      int lane) {
+        bool any = false;
+        uint32_t prev = CONN == 8 ? hmax(jt, hx[0], lane) : jt;
+        uint32_t cur = hmax(J[0], hx[1], lane);
+#pragma unroll
+        for (int r = 0; r < TH; r++) {
+            const uint32_t nxt = r + 1 < TH ? J[r + 1 < TH ? r + 1 : r] : jb;
+            const uint32_t nxtH = hmax(nxt, hx[r + 2], lane);
+            const uint32_t m = max2(cur, max2(prev, CONN == 8 ? nxtH : nxt));
+            any |= min2(I[r], m) != J[r];
+            prev = CONN == 8 ? cur : J[r];
+            cur = nxtH;
+        }
+        return __any_sync(0xffffffffu, any);
+    }
+
+    // For every halo pixel: can one step from the tile's own pixels raise it above its
+    // loaded value? Flag the owning neighbour (misc[(dy + 1) * 3 + dx + 1]).
+    static __device__ void notify_scan(const Smem &s, const uint32_t (&J)[TH], uint32_t jt, uint32_t jb,
+                                       uint32_t it, uint32_t ib, int lane) {
+        if (lane == 0) {
+#pragma unroll
+            for (int r = 0; r < TH; r++) s.col0[r] = J[r] & 0xFFFFu;
+        }
+        if (lane == 31) {
+#pragma unroll
+            for (int r = 0; r < TH; r++) s.col63[r] = J[r] >> 16;
+        }
+        // top and bottom halo rows: the tile's neighbours only (0 beyond its side columns)
+        const uint32_t mt = CONN == 8 ? hmax(J[0], 0u, lane) : J[0];
+        const uint32_t mb = CONN == 8 ? hmax(J[TH - 1], 0u, lane) : J[TH - 1];
+        if (max2(min2(it, mt), jt) != jt) s.misc[1] = 1;
+        if (max2(min2(ib, mb), jb) != jb) s.misc[7] = 1;
+        __syncwarp();
+        // left and right halo columns, one row per lane
+        if (lane < TH) {
+            const int r = lane;
+            uint32_t ml = s.col0[r], mr = s.col63[r];
+            if (CONN == 8) {
+                if (r > 0) { ml = max(ml, s.col0[r - 1]); mr = max(mr, s.col63[r - 1]); }
+                if (r < TH - 1) { ml = max(ml, s.col0[r + 1]); mr = max(mr, s.col63[r + 1]); }
+            }
+            if (min(s.hlI[r + 1], ml) > (s.hxJ[r + 1] >> 16)) s.misc[3] = 1;
+            if (min(s.hrI[r + 1], mr) > s.hxJ[TH + 2 + r + 1]) s.misc[5] = 1;
+        }
+        if (CONN == 8 && lane == 0) {   // corners
+            if (min(s.hlI[0], s.col0[0]) > (s.hxJ[0] >> 16)) s.misc[0] = 1;
+            if (min(s.hlI[TH + 1], s.col0[TH - 1]) > (s.hxJ[TH + 1] >> 16)) s.misc[6] = 1;
+            if (min(s.hrI[0], s.col63[0]) > s.hxJ[TH + 2]) s.misc[2] = 1;
+            if (min(s.hrI[TH + 1], s.col63[TH - 1]) > s.hxJ[2 * TH + 3]) s.misc[8] = 1;
+        }
+    }
+
+    // Store this lane's pairs of the rows it changed.
+    static __device__ void store(const ImageView &im, int y0, int x0, const uint32_t (&J)[TH], uint32_t rows,
+                                 int lane) {
+        const int gx = x0 + 2 * lane;
+        if (gx >= im.W) return;
+        const uint32_t f2 = im.flip | (im.flip << 16);
+        const bool pair = gx + 1 < im.W, vec = pair && (im.W & 1) == 0;
+#pragma unroll
+        for (int r = 0; r < TH; r++) {
+            if (!((rows >> r) & 1u) || y0 + r >= im.H) continue;
+            const size_t e = (size_t)(y0 + r) * im.W + gx;
+            const uint32_t v = J[r] ^ f2;
+            T *q = reinterpret_cast<T *>(im.J) + e;
+            if (vec) {
+                if (sizeof(T) == 1)
+                    __stcg(reinterpret_cast<uint16_t *>(q), (uint16_t)((v & 0xFFu) | ((v >> 8) & 0xFF00u)));
+                else
+                    __stcg(reinterpret_cast<uint32_t *>(q), v);
+            } else {
+                __stcg(q, (T)(v & 0xFFFFu));
+                if (pair) __stcg(q + 1, (T)(v >> 16));
+            }
+        }
+    }
+};
+
+#if IWPP_PHASE_TIMING
+#define IWPP_RT_MARK(k)                         \
+    do {                                        \
+        const long long _n = clock64();         \
+        ph[k] += (unsigned long long)(_n - pt); \
+        pt = _n;                                \
+    } while (0)
+#else
+#define IWPP_RT_MARK(k) \
+    do {                \
+    } while (0)
+#endif
+
+// One visit with the register solver, including the re-processing rounds when the tile
+// is notified while this warp holds it (the protocol of visit_tile).
+template <typename T, int CONN, int TH>
+__device__ void visit_tile_reg(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem, VisitStats &st,
+                               unsigned long long *ph, int lane) {
+    (void)ph;
+#if IWPP_PHASE_TIMING
+    long long pt = clock64();
+#endif
+    using RT = RegTile<T, CONN, TH>;
+    const typename RT::Smem s = RT::carve(wsmem);
+    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const long long c0 = clock64();
+    const uint32_t lt = t - im.tile_base;
+    const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
+    const int y0 = ty * TH, x0 = tx * RT::TW;
+    if (lane < 16) s.misc[lane] = 0;
+    uint32_t J[TH], I[TH], jt, jb, it, ib;
+    RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+    IWPP_RT_MARK(0);
+    uint32_t passes = 0;
+    for (;;) {
+        uint32_t rows = 0;
+        for (;;) {
+            uint32_t ch = RT::pass_down(hx, J, I, jt, lane);
+            ch |= RT::pass_up(hx, J, I, jb, lane);
+            passes += 2;
+            rows |= ch;
+            IWPP_RT_MARK(1);
+            if (!__any_sync(0xffffffffu, ch != 0)) break;
+            const bool more = RT::improvable(hx, J, I, jt, jb, lane);
+            IWPP_RT_MARK(2);
+            if (!more) break;
+        }
+        st.visits++;
+        if (rows) RT::store(im, y0, x0, J, rows, lane);
+        IWPP_RT_MARK(3);
+        RT::notify_scan(s, J, jt, jb, it, ib, lane);
+        IWPP_RT_MARK(4);
+        __threadfence();
+        __syncwarp();
+        IWPP_RT_MARK(5);
+        if (lane < 9 && lane != 4 && s.misc[lane]) {
+            const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
+                notify_tile(a, im.tile_base + (uint32_t)(ny * im.tiles_x + nx));
+        }
+        const bool redo = finish_tile(a, t, lane);
+        IWPP_RT_MARK(6);
+        if (!redo) break;
+        // re-process: J and I stay in registers; only the halo can have changed
+        __syncwarp();
+        if (lane < 16) s.misc[lane] = 0;
+        RT::load_halo(im, s, y0, x0, jt, jb, it, ib, false, lane);
+        IWPP_RT_MARK(7);
+    }
+    st.waves += passes;
+    if (lane == 0 && a.tile_work) {
+        atomicAdd(a.tile_work + t, passes);
+        atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
+    }
+}
+
+__device__ inline void flush_phases(const EngineArgs &a, const unsigned long long (&ph)[8], int lane) {
+#if IWPP_PHASE_TIMING
+    if (lane == 0)
+        for (int k = 0; k < 8; k++) atomicAdd(&a.hdr->phase_cycles[k], ph[k]);
+#else
+    (void)a;
+    (void)ph;
+    (void)lane;
+#endif
+}
+
+template <typename T, int CONN, int TH>
+__global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_reg_kernel(EngineArgs a) {
+    using RT = RegTile<T, CONN, TH>;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wsmem = smem_raw + warp * RT::smem_per_warp(0);
+    VisitStats st = {0, 0, 0, 0};
+    unsigned long long idle = 0, busy = 0, ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (;;) {
+        bool first;
+        const uint32_t t = acquire_tile(a, first, idle, lane);
+        if (t == kDone) break;
+        const unsigned long long b0 = globaltimer_ns();
+        visit_tile_reg<T, CONN, TH>(a, image_of(a, t), t, wsmem, st, ph, lane);
+        busy += globaltimer_ns() - b0;
+    }
+    flush_stats(a, st, idle, busy, lane);
+    flush_phases(a, ph, lane);
+}
+
+// Batch of images of mixed pixel types and connectivities: dispatch on the image's kind.
+template <int TH>
+__global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_reg_mixed_kernel(EngineArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wsmem = smem_raw + warp * RegTile<uint16_t, 8, TH>::smem_per_warp(0);
+    VisitStats st = {0, 0, 0, 0};
+    unsigned long long idle = 0, busy = 0, ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (;;) {
+        bool first;
+        const uint32_t t = acquire_tile(a, first, idle, lane);
+        if (t == kDone) break;
+        const unsigned long long b0 = globaltimer_ns();
+        const ImageView &im = image_of(a, t);
+        switch (im.kind) {
+            case 0: visit_tile_reg<uint8_t, 4, TH>(a, im, t, wsmem, st, ph, lane); break;
+            case 1: visit_tile_reg<uint16_t, 4, TH>(a, im, t, wsmem, st, ph, lane); break;
+            case 2: visit_tile_reg<uint8_t, 8, TH>(a, im, t, wsmem, st, ph, lane); break;
+            default: visit_tile_reg<uint16_t, 8, TH>(a, im, t, wsmem, st, ph, lane); break;
+        }
+        busy += globaltimer_ns() - b0;
+    }
+    flush_stats(a, st, idle, busy, lane);
+    flush_phases(a, ph, lane);
+}
+
+}  // namespace iwpp

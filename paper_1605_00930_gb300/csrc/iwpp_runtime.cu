@@ -54,7 +54,8 @@ static int graph_create(const iwpp_image *imgs, int n, const iwpp_plan *plan, co
 // ---- autotuner ---------------------------------------------------------------------------------
 // Times candidate plans on the batch itself and keeps the fastest. Markers are backed up
 // before and restored before every trial and at the end, so the caller's images are
-// unchanged. Coordinate descent: tile shape, then sweep count, then shared queue capacity.
+// unchanged. Coordinate descent: local solver with its tile shape, then sweep count, then
+// (queue solver only) shared queue capacity.
 struct Tuner {
     const iwpp_image *imgs;
     int n;
@@ -165,7 +166,8 @@ static bool cache_lookup(const char *path, const std::string &key, iwpp_plan *p)
     while (fgets(line, sizeof line, f)) {
         char k[300];
         iwpp_plan q = *p;
-        if (sscanf(line, "%299s %d %d %d %d", k, &q.tile_h, &q.tile_w, &q.sweeps, &q.smem_queue_cap) == 5 &&
+        if (sscanf(line, "%299s %d %d %d %d %d", k, &q.tile_h, &q.tile_w, &q.sweeps, &q.smem_queue_cap,
+                   &q.local_solver) == 6 &&
             key == k && plan_valid(q)) {
             *p = q;   // the last matching line wins
             found = true;
@@ -179,7 +181,8 @@ static void cache_store(const char *path, const std::string &key, const iwpp_pla
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d\n", key.c_str(), p.tile_h, p.tile_w, p.sweeps, p.smem_queue_cap);
+    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), p.tile_h, p.tile_w, p.sweeps, p.smem_queue_cap,
+            p.local_solver);
     fclose(f);
 }
 
@@ -211,14 +214,18 @@ int autotune(const iwpp_image *imgs, int n, iwpp_plan *plan, int reps, const cha
             best = c;
         }
     };
-    static const int shapes[3][2] = {{32, 32}, {32, 64}, {64, 64}};
+    // {tile_h, tile_w, local_solver}
+    static const int shapes[5][3] = {{16, 64, IWPP_SOLVER_REGISTER}, {32, 32, IWPP_SOLVER_QUEUE},
+                                     {32, 64, IWPP_SOLVER_QUEUE}, {64, 64, IWPP_SOLVER_QUEUE},
+                                     {16, 64, IWPP_SOLVER_QUEUE}};
     iwpp_plan base = best;
     for (const auto &sh : shapes) {
         iwpp_plan c = base;
         c.tile_h = sh[0];
         c.tile_w = sh[1];
+        c.local_solver = sh[2];
         if (c.smem_queue_cap > c.tile_h * c.tile_w) c.smem_queue_cap = c.tile_h * c.tile_w;
-        if (c.tile_h == base.tile_h && c.tile_w == base.tile_w) continue;
+        if (c.tile_h == base.tile_h && c.tile_w == base.tile_w && c.local_solver == base.local_solver) continue;
         consider(c);
     }
     base = best;
@@ -230,6 +237,7 @@ int autotune(const iwpp_image *imgs, int n, iwpp_plan *plan, int reps, const cha
     }
     base = best;
     for (int qc : {128, 256, 512, 1024, 2048}) {
+        if (base.local_solver != IWPP_SOLVER_QUEUE) break;   // the register solver has no queues
         if (qc == base.smem_queue_cap || qc > base.tile_h * base.tile_w) continue;
         iwpp_plan c = base;
         c.smem_queue_cap = qc;

@@ -19,6 +19,7 @@ IWPP_DILATE, IWPP_ERODE = 0, 1
 STATUS = {0: "IWPP_OK", 1: "IWPP_ERR_ARG", 2: "IWPP_ERR_PRECONDITION", 3: "IWPP_ERR_WORKSPACE",
           4: "IWPP_ERR_QUEUE_FULL", 5: "IWPP_ERR_TIMEOUT", 6: "IWPP_ERR_CUDA", 7: "IWPP_ERR_INTERNAL"}
 OPS = {"dilate": IWPP_DILATE, "erode": IWPP_ERODE}
+IWPP_SOLVER_QUEUE, IWPP_SOLVER_REGISTER = 0, 1
 
 
 class IwppError(RuntimeError):
@@ -30,7 +31,8 @@ class IwppError(RuntimeError):
 class Plan(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("sweeps", ctypes.c_int32),
                 ("revisit_sweeps", ctypes.c_int32), ("smem_queue_cap", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("watchdog_ns", ctypes.c_int64)]
+                ("blocks_per_sm", ctypes.c_int32), ("local_solver", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("watchdog_ns", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -48,7 +48,7 @@ def test_default_plan_and_shapes(iwpp):
     p = iwpp.iwpp_default_plan()
     assert iwpp.iwpp_tile_shape_supported(p.tile_h, p.tile_w)
     assert p.sweeps >= 0 and 16 <= p.smem_queue_cap <= p.tile_h * p.tile_w
-    for shape in [(32, 32), (32, 64), (64, 64)]:
+    for shape in [(32, 32), (32, 64), (64, 64), (16, 32), (16, 64)]:
         assert iwpp.iwpp_tile_shape_supported(*shape)
     assert not iwpp.iwpp_tile_shape_supported(48, 48)
 
@@ -77,6 +77,12 @@ def test_host_argument_errors_return_before_any_launch(iwpp):
     p = iwpp.iwpp_default_plan()
     p.smem_queue_cap = 8
     assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
+    # the register solver needs 64-column tiles of at most 16 rows; unknown solvers and a
+    # non-zero reserved field are rejected
+    for th, tw, solver, reserved in [(32, 32, 1, 0), (32, 64, 1, 0), (16, 64, 2, 0), (16, 64, 1, 1)]:
+        p = iwpp.iwpp_default_plan()
+        p.tile_h, p.tile_w, p.local_solver, p.reserved = th, tw, solver, reserved
+        assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
     # missing / misaligned workspace
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, null, 16, null) == 3
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, P(ws + 16), 16, null) == 3
@@ -101,7 +107,7 @@ def test_batch_tile_count_is_host_only(iwpp):
     for i, (H, W) in enumerate([(1, 1), (33, 64), (100, 31)]):
         imgs[i] = P(a16, a16, H, W, 8, 0, 0, 0)
     p = iwpp.iwpp_default_plan()
-    p.tile_h, p.tile_w = 32, 32
+    p.tile_h, p.tile_w, p.local_solver = 32, 32, iwpp.IWPP_SOLVER_QUEUE
     assert iwpp.iwpp_batch_tile_count(imgs, p) == 1 + 2 * 2 + 4 * 1
     imgs[1].connectivity = 6
     assert iwpp.iwpp_batch_tile_count(imgs, p) == -1

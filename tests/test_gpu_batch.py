@@ -58,13 +58,35 @@ def _check(oracle_lib, cases, outs):
                                  f"{len(bad)} mismatches, first at {tuple(bad[0])}")
 
 
-@pytest.mark.parametrize("tile", [(32, 32), (32, 64), (64, 64)])
-def test_mixed_batch_static(iw, oracle_lib, tile):
+@pytest.mark.parametrize("tile,solver", [((32, 32), 0), ((32, 64), 0), ((64, 64), 0), ((16, 32), 0),
+                                         ((16, 64), 0), ((16, 64), 1)])
+def test_mixed_batch_static(iw, oracle_lib, tile, solver):
     cases = _mixed_cases(5, 24)
     p = iw.iwpp_default_plan()
     p.tile_h, p.tile_w = tile
+    p.local_solver = solver
     outs, _, _ = _run_batch(iw, cases, p)
     _check(oracle_lib, cases, outs)
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_uniform_batch_each_kind(iw, oracle_lib, solver):
+    """Batches whose images share pixel type and connectivity use the specialised kernels."""
+    p = iw.iwpp_default_plan()
+    p.tile_h, p.tile_w = (32, 32) if solver == 0 else (16, 64)
+    p.local_solver = solver
+    for k, (dtype, conn) in enumerate([(np.uint8, 4), (np.uint16, 4), (np.uint8, 8), (np.uint16, 8)]):
+        cases = []
+        for i, (H, W) in enumerate([(77, 301), (256, 64), (19, 1000)]):
+            field = synth.blob_field_u8(H, W, 6, synth.rng_for(95, 10 * k + i))
+            mask = field if dtype == np.uint8 else synth.to_u16(field)
+            if i % 2:
+                cases.append(synth.Case(synth.fillholes_marker(mask), mask, conn, "erode"))
+            else:
+                cases.append(synth.Case(synth.hdome_marker(mask, 20 if dtype == np.uint8 else 5000), mask, conn,
+                                        "dilate"))
+        outs, _, _ = _run_batch(iw, cases, p)
+        _check(oracle_lib, cases, outs)
 
 
 def test_mixed_batch_random_schedule(iw, oracle_lib):

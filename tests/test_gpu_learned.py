@@ -106,15 +106,17 @@ def test_schedule_is_a_largest_first_permutation(iw):
     iw.iwpp_schedule_from_predictions(B.descs, None, torch.from_numpy(preds).cuda(), order, sweeps, sws)
     o = order.cpu().numpy()
     assert np.array_equal(np.sort(o), np.arange(B.ntiles))
-    # tile -> block map (32 x 32 tiles inside 64 x 64 blocks), image by image
+    # tile -> block map (the default plan's tiles inside 64 x 64 blocks), image by image
+    plan = iw.iwpp_default_plan()
+    th, tw = plan.tile_h, plan.tile_w
     blk = []
     bbase = 0
     for c in cases:
         H, W = c.mask.shape
-        tx, ty = (W + 31) // 32, (H + 31) // 32
+        tx, ty = (W + tw - 1) // tw, (H + th - 1) // th
         nbx = (W + 63) // 64
         for t in range(tx * ty):
-            blk.append(bbase + (t // tx) // 2 * nbx + (t % tx) // 2)
+            blk.append(bbase + ((t // tx) * th) // 64 * nbx + ((t % tx) * tw) // 64)
         bbase += nbx * ((H + 63) // 64)
     blk = np.array(blk)
     keys = np.clip((preds[blk, 0] * 64).astype(np.int64), 0, 1023)

@@ -73,15 +73,39 @@ def _random_pair(rng, H, W, dtype, op, vmax):
 SHAPES = [(1, 1), (1, 700), (700, 1), (32, 32), (64, 64), (65, 130), (129, 65), (200, 333), (257, 513)]
 
 
+# The two local solvers of the persistent kernel, each on a tile shape it supports.
+SOLVERS = {"queue": dict(local_solver=0, tile_h=32, tile_w=32),
+           "register": dict(local_solver=1, tile_h=16, tile_w=64)}
+
+
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 @pytest.mark.parametrize("op", ["dilate", "erode"])
 @pytest.mark.parametrize("conn", [4, 8])
-def test_random_small(iw, oracle_lib, shape, dtype, op, conn):
+def test_random_small(iw, oracle_lib, shape, dtype, op, conn, solver):
     rng = np.random.default_rng([101, shape[0], shape[1], conn, op == "erode"])
+    p = _plan(iw, **SOLVERS[solver])
     for vmax in (7, synth.maxval(dtype)):
         marker, mask = _random_pair(rng, *shape, dtype, op, vmax)
-        check(iw, oracle_lib, marker, mask, conn, op)
+        check(iw, oracle_lib, marker, mask, conn, op, p)
+
+
+# Widths around the 64-column register tile and its 2-pixel pairs (odd widths take the
+# unaligned load path), heights around its 16 rows.
+EDGE_SHAPES = [(15, 63), (16, 64), (17, 65), (33, 127), (31, 128), (16, 129), (2, 2), (3, 1), (1, 3)]
+
+
+@pytest.mark.parametrize("shape", EDGE_SHAPES)
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_register_solver_edges(iw, oracle_lib, shape, dtype, op):
+    rng = np.random.default_rng([102, shape[0], shape[1], op == "erode"])
+    p = _plan(iw, **SOLVERS["register"])
+    for conn in (4, 8):
+        for vmax in (3, synth.maxval(dtype)):
+            marker, mask = _random_pair(rng, *shape, dtype, op, vmax)
+            check(iw, oracle_lib, marker, mask, conn, op, p)
 
 
 @pytest.mark.parametrize("case", load_hand_cases(), ids=lambda c: c["name"])
@@ -91,12 +115,22 @@ def test_hand_cases_gpu(iw, case):
         np.testing.assert_array_equal(got, case["expected"])
 
 
-@pytest.mark.parametrize("tile", [(32, 32), (32, 64), (64, 64)])
+@pytest.mark.parametrize("tile", [(32, 32), (32, 64), (64, 64), (16, 32), (16, 64)])
 @pytest.mark.parametrize("sweeps", [0, 1, 3])
 @pytest.mark.parametrize("qcap", [16, 1024])
 def test_plans_tissue(iw, oracle_lib, tile, sweeps, qcap):
     c = synth.tissue_case(301, 517, nblobs=30)
-    p = _plan(iw, tile_h=tile[0], tile_w=tile[1], sweeps=sweeps, smem_queue_cap=min(qcap, tile[0] * tile[1]))
+    p = _plan(iw, tile_h=tile[0], tile_w=tile[1], sweeps=sweeps, smem_queue_cap=min(qcap, tile[0] * tile[1]),
+              local_solver=0)
+    for conn in (4, 8):
+        check(iw, oracle_lib, c.marker, c.mask, conn, "dilate", p)
+
+
+@pytest.mark.parametrize("sweeps", [0, 1, 3])
+@pytest.mark.parametrize("bps", [0, 1])
+def test_plans_tissue_register(iw, oracle_lib, sweeps, bps):
+    c = synth.tissue_case(301, 517, nblobs=30)
+    p = _plan(iw, sweeps=sweeps, blocks_per_sm=bps, **SOLVERS["register"])
     for conn in (4, 8):
         check(iw, oracle_lib, c.marker, c.mask, conn, "dilate", p)
 
@@ -115,10 +149,12 @@ def test_noise_blur_512(iw, oracle_lib):
     check(iw, oracle_lib, c.marker, c.mask, c.conn, c.op)
 
 
+@pytest.mark.parametrize("solver", [None, "queue", "register"])
 @pytest.mark.parametrize("conn", [4, 8])
-def test_tissue_4096(iw, oracle_lib, conn):
+def test_tissue_4096(iw, oracle_lib, conn, solver):
     c = synth.tissue_case(conn=conn)
-    check(iw, oracle_lib, c.marker, c.mask, conn, "dilate")
+    p = _plan(iw, **SOLVERS[solver]) if solver else None
+    check(iw, oracle_lib, c.marker, c.mask, conn, "dilate", p)
 
 
 def test_sparse_seeds_16384(iw, oracle_lib):

@@ -45,7 +45,8 @@ struct KernelSet {
     void (*scan)(EngineArgs);
     void (*drain)(EngineArgs);
     size_t (*smem)(uint32_t);
-    void (*drain_reg)(EngineArgs);   // register-resident local solver (32-wide tiles), else null
+    void (*scan_reg)(EngineArgs);    // register-resident solver (64-wide tiles), else null
+    void (*drain_reg)(EngineArgs);
     size_t (*smem_reg)(uint32_t);
 };
 static constexpr int kMixed = 4;
@@ -57,9 +58,11 @@ static KernelSet make_set() {
     k.drain = drain_kernel<T, CONN, TH, TW>;
     k.smem = &Tile<T, CONN, TH, TW>::smem_bytes;
     if constexpr (TW == 64 && TH <= 16) {
+        k.scan_reg = scan_reg_kernel<T, CONN, TH>;
         k.drain_reg = drain_reg_kernel<T, CONN, TH>;
         k.smem_reg = &RegTile<T, CONN, TH>::smem_bytes;
     } else {
+        k.scan_reg = nullptr;
         k.drain_reg = nullptr;
         k.smem_reg = nullptr;
     }
@@ -81,9 +84,11 @@ static void fill_shape(KernelSet (&row)[5]) {
     row[kMixed].drain = drain_mixed_kernel<TH, TW>;
     row[kMixed].smem = &mixed_smem_bytes<TH, TW>;
     if constexpr (TW == 64 && TH <= 16) {
+        row[kMixed].scan_reg = scan_reg_mixed_kernel<TH>;
         row[kMixed].drain_reg = drain_reg_mixed_kernel<TH>;
         row[kMixed].smem_reg = &RegTile<uint16_t, 8, TH>::smem_bytes;
     } else {
+        row[kMixed].scan_reg = nullptr;
         row[kMixed].drain_reg = nullptr;
         row[kMixed].smem_reg = nullptr;
     }
@@ -124,6 +129,8 @@ static cudaError_t ensure_smem_attr(int shape, int v, size_t bytes) {
     if (k.drain_reg) {
         e = cudaFuncSetAttribute((const void *)k.drain_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute((const void *)k.scan_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e != cudaSuccess) return e;
     }
     done = want;
     return cudaSuccess;
@@ -138,9 +145,13 @@ int device_sm_count() {
     return n;
 }
 
-// The persistent kernel of a plan (queue or register local solver) and its shared memory.
+// The scan and persistent kernels of a plan (queue or register local solver) and their
+// shared memory.
 static void (*drain_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
     return p.local_solver == IWPP_SOLVER_REGISTER ? k.drain_reg : k.drain;
+}
+static void (*scan_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
+    return p.local_solver == IWPP_SOLVER_REGISTER ? k.scan_reg : k.scan;
 }
 static size_t drain_smem(const iwpp_plan &p, const KernelSet &k) {
     return p.local_solver == IWPP_SOLVER_REGISTER ? k.smem_reg((uint32_t)p.smem_queue_cap)
@@ -180,11 +191,13 @@ bool plan_valid(const iwpp_plan &p) {
     return true;
 }
 
-// The measured best static plan: 16 x 64 tiles settled by the register solver.
+// The measured best static plan: 16 x 64 tiles settled by the register solver, no sweeps
+// before the persistent kernel (the scan kernel still checks the precondition and
+// collects the frontier).
 void default_plan(iwpp_plan *p) {
     p->tile_h = 16;
     p->tile_w = 64;
-    p->sweeps = 1;
+    p->sweeps = 0;
     p->revisit_sweeps = 0;
     p->smem_queue_cap = 512;
     p->blocks_per_sm = 0;
@@ -294,7 +307,7 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
         const int sms = device_sm_count();
         const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
         const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
-        k.scan<<<scan_grid, kThreads, smem, stream>>>(a);
+        scan_fn(p, k)<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
     }
     if (phases & kPhaseDrain) drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
@@ -431,7 +444,7 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     const int sms = device_sm_count();
     const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
     const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
-    k.scan<<<scan_grid, kThreads, smem, stream>>>(a);
+    scan_fn(p, k)<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
     const uint32_t cgrid = (L.ntiles + 255) / 256 < (uint32_t)(sms * 8) ? (L.ntiles + 255) / 256 : (uint32_t)(sms * 8);
     compact_kernel<<<cgrid, 256, 0, stream>>>(a);
     finalize_queue_kernel<<<cgrid, 256, 0, stream>>>(a);

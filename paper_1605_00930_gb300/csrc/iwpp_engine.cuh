@@ -162,9 +162,10 @@ __device__ inline bool push_tile(const EngineArgs &a, uint32_t t) {
 }
 
 // Tile t has a pixel that a halo pixel can raise: make it PENDING (queue it if idle).
+// The queue entry is written only after the state change has returned (a control
+// dependency on its old value), so a popper always finds the tile PENDING.
 __device__ inline void notify_tile(const EngineArgs &a, uint32_t t) {
     const uint32_t old = atomicOr(a.state + t, ST_PENDING);
-    __threadfence();   // order the state change before the queue entry that publishes it
     if ((old & (ST_PENDING | ST_ACTIVE)) == 0) {
         atomicAdd(&a.hdr->pending, 1u);
         push_tile(a, t);
@@ -849,20 +850,20 @@ struct VisitStats {
 // End of a visit round (whole warp, after the tile's stores and notifications are
 // fenced): ACTIVE -> IDLE and one fewer pending tile, unless the tile was notified while
 // this warp held it; then it stays ACTIVE and the warp processes it again (returns true).
+// The decrement is issued only once the state change has returned, and it cannot reach
+// zero early: the notified neighbours were counted first, and every tile still being
+// visited is counted too.
 __device__ inline bool finish_tile(const EngineArgs &a, uint32_t t, int lane) {
     uint32_t redo = 0;
     if (lane == 0) {
         const uint32_t busy_st = ST_ACTIVE | ST_VISITED;
         const uint32_t r = atomicCAS(a.state + t, busy_st, ST_VISITED);
         if (r == busy_st) {
-            __threadfence();
             atomicSub(&a.hdr->pending, 1u);
         } else {
             atomicAnd(a.state + t, ~ST_PENDING);   // notified while ACTIVE: go again
-            redo = 1;
+            redo = !fatal(a.hdr);
         }
-        __threadfence();
-        redo = redo && !fatal(a.hdr);
     }
     return __shfl_sync(0xffffffffu, redo, 0) != 0;
 }

@@ -197,6 +197,88 @@ struct RegTile {
         return chg;
     }
 
+    // ---- raster / anti-raster sweeps (Algorithm 7's scanning phase) ------------------------
+    // Along a row, the raster update J(x) <- min(I(x), max(a(x), J(x - 1))) is the map
+    // v -> clamp(v, lo, hi) with lo = min(I, a), hi = I, and clamps compose into clamps, so a
+    // whole row is one warp scan of (lo, hi) pairs packed as u16x2: five shuffle steps
+    // instead of a 64-step chain. a(x) holds the pixel's own value and its neighbours in
+    // the previous row (already swept), so one raster sweep followed by one anti-raster
+    // sweep is exactly the paper's pair of scans over this tile.
+    static __device__ __forceinline__ uint32_t dup_lo(uint32_t g) { return __byte_perm(g, g, 0x1010); }
+    static __device__ __forceinline__ uint32_t dup_hi(uint32_t g) { return __byte_perm(g, g, 0x3232); }
+
+    // West-to-east pass over one packed row. A = min(I, candidates) per pixel, Ir = mask,
+    // hxr = this lane's halo word of the row (lane 0: west halo pixel << 16).
+    static __device__ __forceinline__ uint32_t row_we(uint32_t A, uint32_t Ir, uint32_t hxr, int lane) {
+        // this lane's pair as one clamp, even pixel first: (lo, hi)
+        uint32_t G = min2(dup_hi(Ir), max2(dup_hi(A), __byte_perm(A, Ir, 0x5410)));
+        if (lane == 0) {   // fold the west halo in: lane 0's map becomes a constant
+            const uint32_t c = min(G >> 16, max(G & 0xFFFFu, hxr >> 16));
+            G = c | (c << 16);
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t Q = __shfl_up_sync(0xffffffffu, G, d);
+            const uint32_t C = min2(dup_hi(G), max2(dup_lo(G), Q));   // this map after Q
+            if (lane >= d) G = C;
+        }
+        // every map is now a constant: the value leaving this lane's odd pixel
+        const uint32_t E = __shfl_up_sync(0xffffffffu, G, 1);
+        const uint32_t u = lane == 0 ? hxr >> 16 : E & 0xFFFFu;
+        const uint32_t X = min2(Ir, max2(A, u));                      // even pixel (low half)
+        return __byte_perm(X, G, 0x5410);
+    }
+
+    // East-to-west pass over one packed row (lane 31: east halo pixel in the low half).
+    static __device__ __forceinline__ uint32_t row_ew(uint32_t A, uint32_t Ir, uint32_t hxr, int lane) {
+        uint32_t G = min2(dup_lo(Ir), max2(dup_lo(A), __byte_perm(A, Ir, 0x7632)));   // odd pixel first
+        if (lane == 31) {
+            const uint32_t c = min(G >> 16, max(G & 0xFFFFu, hxr & 0xFFFFu));
+            G = c | (c << 16);
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t Q = __shfl_down_sync(0xffffffffu, G, d);
+            const uint32_t C = min2(dup_hi(G), max2(dup_lo(G), Q));
+            if (lane + d < 32) G = C;
+        }
+        const uint32_t E = __shfl_down_sync(0xffffffffu, G, 1);
+        const uint32_t u = lane == 31 ? hxr & 0xFFFFu : E & 0xFFFFu;
+        const uint32_t Y = min2(Ir, max2(A, u << 16));                // odd pixel (high half)
+        return __byte_perm(G, Y, 0x7610);
+    }
+
+    // Raster sweep: rows top to bottom, each from its own values and the swept row above
+    // (N, and NW / NE for 8-conn), then west to east. Returns this lane's changed rows.
+    static __device__ __forceinline__ uint32_t sweep_raster(const uint32_t *hx, uint32_t (&J)[TH],
+                                                            const uint32_t (&I)[TH], uint32_t jt, int lane) {
+        uint32_t chg = 0, up = jt;
+#pragma unroll
+        for (int r = 0; r < TH; r++) {
+            const uint32_t hu = CONN == 8 ? hmax(up, hx[r], lane) : up;
+            const uint32_t nv = row_we(min2(I[r], max2(J[r], hu)), I[r], hx[r + 1], lane);
+            chg |= (uint32_t)(nv != J[r]) << r;
+            J[r] = nv;
+            up = nv;
+        }
+        return chg;
+    }
+
+    // Anti-raster sweep: rows bottom to top (S, and SW / SE), then east to west.
+    static __device__ __forceinline__ uint32_t sweep_antiraster(const uint32_t *hx, uint32_t (&J)[TH],
+                                                                const uint32_t (&I)[TH], uint32_t jb, int lane) {
+        uint32_t chg = 0, dn = jb;
+#pragma unroll
+        for (int r = TH - 1; r >= 0; r--) {
+            const uint32_t hd = CONN == 8 ? hmax(dn, hx[r + 2], lane) : dn;
+            const uint32_t nv = row_ew(min2(I[r], max2(J[r], hd)), I[r], hx[r + 1], lane);
+            chg |= (uint32_t)(nv != J[r]) << r;
+            J[r] = nv;
+            dn = nv;
+        }
+        return chg;
+    }
+
     // Is some pixel of the tile still below min(I, max over its neighbourhood)? The rows
     // are independent here, so this costs far less latency than another pass pair.
     static __device__ __forceinline__ bool improvable(const uint32_t *hx, const uint32_t (&J)[TH],
@@ -254,31 +336,89 @@ struct RegTile {
         }
     }
 
-    // Store this lane's pairs of the rows it changed.
+    // Store this lane's pairs of the rows it changed (rows below the image never change).
     static __device__ void store(const ImageView &im, int y0, int x0, const uint32_t (&J)[TH], uint32_t rows,
                                  int lane) {
         const int gx = x0 + 2 * lane;
         if (gx >= im.W) return;
         const uint32_t f2 = im.flip | (im.flip << 16);
-        const bool pair = gx + 1 < im.W, vec = pair && (im.W & 1) == 0;
+        T *q = reinterpret_cast<T *>(im.J) + (size_t)y0 * im.W + gx;
+        if (gx + 1 < im.W && (im.W & 1) == 0) {
 #pragma unroll
-        for (int r = 0; r < TH; r++) {
-            if (!((rows >> r) & 1u) || y0 + r >= im.H) continue;
-            const size_t e = (size_t)(y0 + r) * im.W + gx;
-            const uint32_t v = J[r] ^ f2;
-            T *q = reinterpret_cast<T *>(im.J) + e;
-            if (vec) {
-                if (sizeof(T) == 1)
-                    __stcg(reinterpret_cast<uint16_t *>(q), (uint16_t)((v & 0xFFu) | ((v >> 8) & 0xFF00u)));
-                else
-                    __stcg(reinterpret_cast<uint32_t *>(q), v);
-            } else {
-                __stcg(q, (T)(v & 0xFFFFu));
-                if (pair) __stcg(q + 1, (T)(v >> 16));
+            for (int r = 0; r < TH; r++) {
+                const uint32_t v = J[r] ^ f2;
+                if ((rows >> r) & 1u) {
+                    if (sizeof(T) == 1)
+                        __stcg(reinterpret_cast<uint16_t *>(q + (size_t)r * im.W), (uint16_t)__byte_perm(v, 0u, 0x0020));
+                    else
+                        __stcg(reinterpret_cast<uint32_t *>(q + (size_t)r * im.W), v);
+                }
+            }
+        } else {
+            const bool pair = gx + 1 < im.W;
+#pragma unroll
+            for (int r = 0; r < TH; r++) {
+                const uint32_t v = J[r] ^ f2;
+                if ((rows >> r) & 1u) {
+                    __stcg(q + (size_t)r * im.W, (T)(v & 0xFFFFu));
+                    if (pair) __stcg(q + (size_t)r * im.W + 1, (T)(v >> 16));
+                }
             }
         }
     }
 };
+
+#ifndef IWPP_REG_SWEEPS
+#define IWPP_REG_SWEEPS 0   // 1: visits settle tiles with raster / anti-raster sweep pairs
+#endif
+
+// Frontier initialisation of one tile with the tile in registers (the scan kernel's body
+// for the register solver's plans): precondition check, the tile's raster / anti-raster
+// sweep pairs, store, then mark the tile if one of its pixels can still rise and each
+// neighbour one of whose halo pixels it can raise.
+template <typename T, int CONN, int TH>
+__device__ void scan_tile_reg(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem, int lane) {
+    using RT = RegTile<T, CONN, TH>;
+    const typename RT::Smem s = RT::carve(wsmem);
+    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const long long c0 = clock64();
+    const uint32_t lt = t - im.tile_base;
+    const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
+    const int y0 = ty * TH, x0 = tx * RT::TW;
+    if (lane < 16) s.misc[lane] = 0;
+    uint32_t J[TH], I[TH], jt, jb, it, ib;
+    RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
+    bad = __any_sync(0xffffffffu, bad);
+    const int sweeps = a.tile_sweeps ? (int)a.tile_sweeps[t] : a.sweeps;
+    uint32_t rows = 0;
+    for (int k = 0; k < sweeps; k++) {
+        rows |= RT::sweep_raster(hx, J, I, jt, lane);
+        rows |= RT::sweep_antiraster(hx, J, I, jb, lane);
+    }
+    if (rows) RT::store(im, y0, x0, J, rows, lane);
+    const bool active = RT::improvable(hx, J, I, jt, jb, lane);
+    RT::notify_scan(s, J, jt, jb, it, ib, lane);
+    __threadfence();
+    __syncwarp();
+    if (lane < 9 && lane != 4 && s.misc[lane]) {
+        const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+        if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x) {
+            const uint32_t n = im.tile_base + (uint32_t)(ny * im.tiles_x + nx);
+            if (a.defer_push) mark_pending(a, n); else notify_tile(a, n);
+        }
+    }
+    if (lane == 0) {
+        if (active) {
+            if (a.defer_push) mark_pending(a, t); else notify_tile(a, t);
+        }
+        if (bad) set_status(a.hdr, kErrPrecondition);
+        if (a.tile_work) atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
+    }
+    __syncwarp();
+}
 
 #if IWPP_PHASE_TIMING
 #define IWPP_RT_MARK(k)                         \
@@ -317,8 +457,13 @@ __device__ void visit_tile_reg(const EngineArgs &a, const ImageView &im, uint32_
     for (;;) {
         uint32_t rows = 0;
         for (;;) {
+#if IWPP_REG_SWEEPS
+            uint32_t ch = RT::sweep_raster(hx, J, I, jt, lane);
+            ch |= RT::sweep_antiraster(hx, J, I, jb, lane);
+#else
             uint32_t ch = RT::pass_down(hx, J, I, jt, lane);
             ch |= RT::pass_up(hx, J, I, jb, lane);
+#endif
             passes += 2;
             rows |= ch;
             IWPP_RT_MARK(1);
@@ -385,6 +530,34 @@ __global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_reg_kernel(En
     }
     flush_stats(a, st, idle, busy, lane);
     flush_phases(a, ph, lane);
+}
+
+template <typename T, int CONN, int TH>
+__global__ void __launch_bounds__(kThreads) scan_reg_kernel(EngineArgs a) {
+    using RT = RegTile<T, CONN, TH>;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wsmem = smem_raw + warp * RT::smem_per_warp(0);
+    const uint32_t nworkers = gridDim.x * kWarpsPerCta;
+    for (uint32_t t = blockIdx.x * kWarpsPerCta + warp; t < a.ntiles; t += nworkers)
+        scan_tile_reg<T, CONN, TH>(a, image_of(a, t), t, wsmem, lane);
+}
+
+template <int TH>
+__global__ void __launch_bounds__(kThreads) scan_reg_mixed_kernel(EngineArgs a) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wsmem = smem_raw + warp * RegTile<uint16_t, 8, TH>::smem_per_warp(0);
+    const uint32_t nworkers = gridDim.x * kWarpsPerCta;
+    for (uint32_t t = blockIdx.x * kWarpsPerCta + warp; t < a.ntiles; t += nworkers) {
+        const ImageView &im = image_of(a, t);
+        switch (im.kind) {
+            case 0: scan_tile_reg<uint8_t, 4, TH>(a, im, t, wsmem, lane); break;
+            case 1: scan_tile_reg<uint16_t, 4, TH>(a, im, t, wsmem, lane); break;
+            case 2: scan_tile_reg<uint8_t, 8, TH>(a, im, t, wsmem, lane); break;
+            default: scan_tile_reg<uint16_t, 8, TH>(a, im, t, wsmem, lane); break;
+        }
+    }
 }
 
 // Batch of images of mixed pixel types and connectivities: dispatch on the image's kind.

@@ -241,8 +241,11 @@ def run_ours(args, rank: int, world: int):
     peak, peak_kind = _peaks()
     s = bytes_per_px[0]
     nl = len(dev_cases)
-    dominant = "drain_kernel" if drain_ms >= scan_ms else "scan_kernel"
-    dom_ms = (drain_ms if dominant == "drain_kernel" else scan_ms) / (args.steps * nl)
+    plan = iwpp.iwpp_default_plan()
+    reg = plan.local_solver == iwpp.IWPP_SOLVER_REGISTER
+    drain_name, scan_name = ("drain_reg_kernel", "scan_reg_kernel") if reg else ("drain_kernel", "scan_kernel")
+    dominant = drain_name if drain_ms >= scan_ms else scan_name
+    dom_ms = (drain_ms if dominant == drain_name else scan_ms) / (args.steps * nl)
     alg_bytes = 3 * s * cases[0][1].size   # compulsory bytes of one reconstruction: read J, I, write J
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     traffic = _traffic_from_profiles(dominant)
@@ -253,12 +256,12 @@ def run_ours(args, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": desc, "pixels_per_step": pix_per_step, "form": "plain per-image",
-                   "plan": iwpp.iwpp_default_plan().as_dict(),
+                   "plan": plan.as_dict(),
                    "l2": "flushed before every timed step (256 MiB write)",
                    "timing": "CUDA events around the scan and drain launches of each step",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "phases_ms_per_step": {"scan_kernel": round(scan_ms / args.steps, 4),
-                               "drain_kernel": round(drain_ms / args.steps, 4)},
+        "phases_ms_per_step": {scan_name: round(scan_ms / args.steps, 4),
+                               drain_name: round(drain_ms / args.steps, 4)},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
                      "traffic": traffic,

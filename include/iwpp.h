@@ -204,7 +204,8 @@ IWPP_API int iwpp_reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_pl
  *   tile_sweeps  uint8[ntiles]: raster / anti-raster sweep pairs of each tile in
  *                the scan kernel (else plan->sweeps for every tile)
  *   tile_work    uint32[2 * ntiles], caller-zeroed: receives per-tile work, [t] =
- *                wave-queue pops, [ntiles + t] = SM cycles spent on the tile
+ *                wave-queue pops (queue solver) or row passes (register
+ *                solver), [ntiles + t] = SM cycles spent on the tile
  * The schedule changes the work done, never the result.
  */
 IWPP_API int iwpp_reconstruct_batch_sched(const iwpp_image *imgs, int n, const iwpp_plan *plan,
@@ -259,8 +260,8 @@ IWPP_API int iwpp_autotune_batch(const iwpp_image *imgs, int n, iwpp_plan *plan_
  *   [15]     log2(pixels in the block) / 12
  * The MLP is 16 -> 64 -> 64 -> 2 with ReLU, FP32, IWPP_MLP_PARAMS parameters in
  * one flat device array: W1[16][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]
- * (y = x W + b). Output 0 predicts log(1 + wave-queue pops) of the block, output
- * 1 the raster / anti-raster sweep pairs to run on its tiles.
+ * (y = x W + b). Output 0 predicts the block's log work, log(1 + SM cycles spent
+ * on its tiles), output 1 the raster / anti-raster sweep pairs to run on them.
  * The paper has no learned schedule; none of these calls can change a
  * reconstruction result, they only order the work.
  */
@@ -312,7 +313,8 @@ IWPP_API int iwpp_schedule_learned(const iwpp_image *imgs, int n, const iwpp_pla
                                    size_t sws_bytes, void *stream);
 
 /* Per-tile work from iwpp_reconstruct_batch_sched summed into blocks:
- * block_work[b] = pops, block_work[nblocks + b] = SM cycles (caller-zeroed uint64). */
+ * block_work[b] = pops or passes, block_work[nblocks + b] = SM cycles (caller-zeroed
+ * uint64). */
 IWPP_API int iwpp_tile_work_to_blocks(const iwpp_image *imgs, int n, const iwpp_plan *plan,
                                       const uint32_t *tile_work, unsigned long long *block_work,
                                       void *sched_ws, size_t sws_bytes, void *stream);
@@ -349,7 +351,8 @@ IWPP_API int iwpp_reconstruct_noalloc(void *marker_inout, const void *mask, int6
 /*
  * Work counters of the last call (single image or batch) that used `workspace`: tile
  * visits by the persistent kernel, wave-queue entries processed (pops),
- * entries created by the visits' initial scans (seeds), wave steps run, and
+ * entries created by the visits' initial scans (seeds), wave steps run (row
+ * passes for the register solver), and
  * the persistent workers' summed waiting time and processing time in ns.
  * Host pointer out[6]. Synchronises `stream`. Returns IWPP_OK or IWPP_ERR_CUDA.
  */

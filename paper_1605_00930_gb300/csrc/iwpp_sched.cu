@@ -317,7 +317,8 @@ __global__ void sched_scatter_kernel(uint32_t ntiles, const uint16_t *key, uint3
         order[atomicAdd(cursor + key[t], 1u)] = t;
 }
 
-// Per-tile work (pops, cycles) summed into feature blocks: out[b] = pops, out[nblocks + b] = cycles.
+// Per-tile work (pops or passes, cycles) summed into feature blocks: out[b] = pops or passes,
+// out[nblocks + b] = cycles.
 __global__ void tile_work_blocks_kernel(const SchedImage *tab, int nimg, uint32_t ntiles, uint32_t nblocks, int th,
                                         int tw, const uint32_t *tile_work, unsigned long long *out) {
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {

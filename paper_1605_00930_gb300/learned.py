@@ -6,8 +6,10 @@ this module only drives it through the C ABI:
 
   * labels come from runs of the reconstruction itself: for every sweep count s of
     SWEEP_OPTIONS the batch is reconstructed with every tile forced to s sweeps and
-    per-tile work counters on; per 64 x 64 block the label is log(1 + pops) of the
-    s = 1 run and the s with the fewest SM cycles spent on the block's tiles;
+    per-tile work counters on; per 64 x 64 block the work label is log(1 + SM cycles spent
+    on the block's tiles) in the run with the plan's own sweep count, and the sweep label
+    is the smallest s that no larger option beats by more than SWEEP_MARGIN (cycle counts
+    of single runs are noisy; extra sweeps must pay for themselves clearly);
   * training runs the library's hand-written FP32 backpropagation and Adam kernels;
   * weights are saved as raw float32 plus a JSON header; a missing or corrupt file
     means the static schedule is used.
@@ -23,7 +25,8 @@ import numpy as np
 from . import iwpp
 
 SWEEP_OPTIONS = (0, 1, 2, 4, 8)
-WEIGHTS_VERSION = 1
+SWEEP_MARGIN = 0.25
+WEIGHTS_VERSION = 2
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -60,10 +63,22 @@ def features(items, device="cuda"):
     return feats
 
 
+def sweep_label(cycles, options=SWEEP_OPTIONS, margin: float = SWEEP_MARGIN):
+    """Per block (columns of `cycles`, one row per option in increasing order): the smallest
+    option that no larger option beats by more than `margin` of its cycles."""
+    best = np.full(cycles.shape[1], float(options[0]))
+    cur = cycles[0].copy()
+    for oi in range(1, len(options)):
+        better = cycles[oi] < (1.0 - margin) * cur
+        best = np.where(better, float(options[oi]), best)
+        cur = np.where(better, cycles[oi], cur)
+    return best
+
+
 def block_labels(items, plan=None, options=SWEEP_OPTIONS, reps: int = 1):
-    """Run the batch once per sweep option with work counters; returns (log-work label of
-    the s = 1 run, best sweep option per block, cycles per option) as numpy arrays. The
-    markers are restored after every run."""
+    """Run the batch once per sweep option with work counters; returns (log-work label:
+    log(1 + cycles) of the run with the plan's sweep count, sweep label per block, cycles
+    per option) as numpy arrays. The markers are restored after every run."""
     import torch
     init = [m.clone() for m, _, _, _ in items]
     B = iwpp.Batch(items, plan)
@@ -71,7 +86,7 @@ def block_labels(items, plan=None, options=SWEEP_OPTIONS, reps: int = 1):
     nb = iwpp.iwpp_batch_block_count(B.descs)
     sws = iwpp.alloc_workspace(iwpp.iwpp_sched_workspace_bytes(B.descs, plan), init[0].device)
     cycles = np.zeros((len(options), nb))
-    pops1 = None
+    own = (plan if plan is not None else iwpp.iwpp_default_plan()).sweeps
     for oi, s in enumerate(options):
         for _ in range(reps):
             for (m, _, _, _), m0 in zip(items, init):
@@ -85,14 +100,10 @@ def block_labels(items, plan=None, options=SWEEP_OPTIONS, reps: int = 1):
             iwpp.iwpp_tile_work_to_blocks(B.descs, plan, work, bw, sws)
             bw = bw.cpu().numpy().astype(np.float64)
             cycles[oi] += bw[nb:] / reps
-            if s == 1 and pops1 is None:
-                pops1 = bw[:nb]
     for (m, _, _, _), m0 in zip(items, init):
         m.copy_(m0)
-    if pops1 is None:
-        pops1 = np.zeros(nb)
-    best = np.asarray(options, dtype=np.float64)[np.argmin(cycles, axis=0)]
-    return np.log1p(pops1), best, cycles
+    oi = options.index(own) if own in options else 0
+    return np.log1p(cycles[oi]), sweep_label(cycles, options), cycles
 
 
 class LearnedScheduler:

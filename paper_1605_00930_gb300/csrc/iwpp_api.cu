@@ -532,6 +532,23 @@ extern "C" int iwpp_sync_status(const void *workspace, void *stream) {
     return (int)st;
 }
 
+#if IWPP_TRACE
+// Measurement builds only: copy out and reset the visit trace of the register solver
+// (hist: uint32[16384] visits started per 10 us; returns the longest chain of tile hops).
+extern "C" IWPP_API int iwpp_trace_read(unsigned int *hist_host) {
+    unsigned int mg = 0;
+    cudaMemcpyFromSymbol(&mg, iwpp::g_trace_maxgen, sizeof mg);
+    if (hist_host) cudaMemcpyFromSymbol(hist_host, iwpp::g_trace_hist, sizeof(unsigned int) * iwpp::kTraceBins);
+    static unsigned int zeros[iwpp::kTraceBins];
+    cudaMemcpyToSymbol(iwpp::g_trace_hist, zeros, sizeof zeros);
+    const unsigned int z = 0;
+    cudaMemcpyToSymbol(iwpp::g_trace_maxgen, &z, sizeof z);
+    const unsigned long long big = ~0ull;
+    cudaMemcpyToSymbol(iwpp::g_trace_t0, &big, sizeof big);
+    return (int)mg;
+}
+#endif
+
 extern "C" int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[6]) {
     if (!workspace || !out) return IWPP_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -368,6 +368,20 @@ struct RegTile {
     }
 };
 
+#ifndef IWPP_TRACE
+#define IWPP_TRACE 0   // record visit generations and a start-time histogram (measurement builds)
+#endif
+#if IWPP_TRACE
+// Generation of a visit = 1 + the largest generation among the visits that notified the
+// tile; the largest generation is the longest chain of tile hops. Visit start times are
+// binned in 10 us steps from the first visit of the launch.
+constexpr int kTraceTiles = 1 << 22, kTraceBins = 1 << 14;
+__device__ unsigned int g_trace_gen[kTraceTiles];
+__device__ unsigned int g_trace_hist[kTraceBins];
+__device__ unsigned long long g_trace_t0;
+__device__ unsigned int g_trace_maxgen;
+#endif
+
 #ifndef IWPP_REG_SWEEPS
 #define IWPP_REG_SWEEPS 0   // 1: visits settle tiles with raster / anti-raster sweep pairs
 #endif
@@ -386,6 +400,9 @@ __device__ void scan_tile_reg(const EngineArgs &a, const ImageView &im, uint32_t
     const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
     const int y0 = ty * TH, x0 = tx * RT::TW;
     if (lane < 16) s.misc[lane] = 0;
+#if IWPP_TRACE
+    if (lane == 0 && t < (uint32_t)kTraceTiles) g_trace_gen[t] = 0;
+#endif
     uint32_t J[TH], I[TH], jt, jb, it, ib;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
     bool bad = false;
@@ -450,6 +467,18 @@ __device__ void visit_tile_reg(const EngineArgs &a, const ImageView &im, uint32_
     const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
     const int y0 = ty * TH, x0 = tx * RT::TW;
     if (lane < 16) s.misc[lane] = 0;
+#if IWPP_TRACE
+    uint32_t gen = 0;
+    if (lane == 0) {
+        const unsigned long long now = globaltimer_ns();
+        atomicMin(&g_trace_t0, now);
+        const unsigned long long b = (now - *(volatile unsigned long long *)&g_trace_t0) / 10000ull;
+        atomicAdd(&g_trace_hist[b < (unsigned long long)kTraceBins ? b : kTraceBins - 1], 1u);
+        gen = (t < (uint32_t)kTraceTiles ? *(volatile unsigned int *)&g_trace_gen[t] : 0u) + 1u;
+        atomicMax(&g_trace_maxgen, gen);
+    }
+    gen = __shfl_sync(0xffffffffu, gen, 0);
+#endif
     uint32_t J[TH], I[TH], jt, jb, it, ib;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
     IWPP_RT_MARK(0);
@@ -482,8 +511,13 @@ __device__ void visit_tile_reg(const EngineArgs &a, const ImageView &im, uint32_
         IWPP_RT_MARK(5);
         if (lane < 9 && lane != 4 && s.misc[lane]) {
             const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
-            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
-                notify_tile(a, im.tile_base + (uint32_t)(ny * im.tiles_x + nx));
+            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x) {
+                const uint32_t n = im.tile_base + (uint32_t)(ny * im.tiles_x + nx);
+#if IWPP_TRACE
+                if (n < (uint32_t)kTraceTiles) atomicMax(&g_trace_gen[n], gen);
+#endif
+                notify_tile(a, n);
+            }
         }
         const bool redo = finish_tile(a, t, lane);
         IWPP_RT_MARK(6);

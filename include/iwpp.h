@@ -79,7 +79,9 @@ typedef enum {
  *                      of a warp; waves larger than this spill into the
  *                      warp's global overflow queue (16 .. tile_h * tile_w)
  *   blocks_per_sm      persistent-kernel CTAs (of 4 warps) per SM
- *                      (0 = occupancy maximum)
+ *                      (0 = occupancy maximum); register-solver plans asking
+ *                      for more than 4 use a build of the persistent kernel
+ *                      with fewer registers per thread that fits 6
  *   local_solver       how the persistent kernel settles a tile it visits:
  *                      IWPP_SOLVER_QUEUE, the FIFO wave queues of Algorithm
  *                      7's queue phase in shared memory, or
@@ -231,7 +233,8 @@ IWPP_API int iwpp_graph_destroy(iwpp_graph graph);
 
 /*
  * Autotuner: picks the local solver with its tile shape, the sweep count and
- * (queue solver) the shared queue capacity of *plan_inout by timing candidate
+ * (register solver) the CTAs per SM or (queue solver) the shared queue
+ * capacity of *plan_inout by timing candidate
  * plans on the batch itself (coordinate descent
  * from the given plan; best of `reps` runs each, each after writing a buffer of
  * twice the L2 size; CUDA events on `stream`). The

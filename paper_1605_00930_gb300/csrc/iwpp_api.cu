@@ -21,7 +21,6 @@
 
 #include "../../include/iwpp.h"
 #include "iwpp_engine.cuh"
-#include "iwpp_regtile.cuh"
 #include "iwpp_host.h"
 
 namespace iwpp {
@@ -45,9 +44,7 @@ struct KernelSet {
     void (*scan)(EngineArgs);
     void (*drain)(EngineArgs);
     size_t (*smem)(uint32_t);
-    void (*scan_reg)(EngineArgs);    // register-resident solver (64-wide tiles), else null
-    void (*drain_reg)(EngineArgs);
-    size_t (*smem_reg)(uint32_t);
+    RegKernelSet reg;                // register local solver (16 x 64 tiles), else null
 };
 static constexpr int kMixed = 4;
 
@@ -57,15 +54,7 @@ static KernelSet make_set() {
     k.scan = scan_kernel<T, CONN, TH, TW>;
     k.drain = drain_kernel<T, CONN, TH, TW>;
     k.smem = &Tile<T, CONN, TH, TW>::smem_bytes;
-    if constexpr (TW == 64 && TH <= 16) {
-        k.scan_reg = scan_reg_kernel<T, CONN, TH>;
-        k.drain_reg = drain_reg_kernel<T, CONN, TH>;
-        k.smem_reg = &RegTile<T, CONN, TH>::smem_bytes;
-    } else {
-        k.scan_reg = nullptr;
-        k.drain_reg = nullptr;
-        k.smem_reg = nullptr;
-    }
+    k.reg = reg_kernel_set(TH, TW, (sizeof(T) == 2 ? 1 : 0) | (CONN == 8 ? 2 : 0));
     return k;
 }
 
@@ -83,15 +72,7 @@ static void fill_shape(KernelSet (&row)[5]) {
     row[kMixed].scan = scan_mixed_kernel<TH, TW>;
     row[kMixed].drain = drain_mixed_kernel<TH, TW>;
     row[kMixed].smem = &mixed_smem_bytes<TH, TW>;
-    if constexpr (TW == 64 && TH <= 16) {
-        row[kMixed].scan_reg = scan_reg_mixed_kernel<TH>;
-        row[kMixed].drain_reg = drain_reg_mixed_kernel<TH>;
-        row[kMixed].smem_reg = &RegTile<uint16_t, 8, TH>::smem_bytes;
-    } else {
-        row[kMixed].scan_reg = nullptr;
-        row[kMixed].drain_reg = nullptr;
-        row[kMixed].smem_reg = nullptr;
-    }
+    row[kMixed].reg = reg_kernel_set(TH, TW, kMixed);
 }
 
 static KernelSet g_sets[kNumShapes][5];
@@ -126,10 +107,9 @@ static cudaError_t ensure_smem_attr(int shape, int v, size_t bytes) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute((const void *)k.drain, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     if (e != cudaSuccess) return e;
-    if (k.drain_reg) {
-        e = cudaFuncSetAttribute((const void *)k.drain_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute((const void *)k.scan_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    for (void (*f)(EngineArgs) : {k.reg.scan, k.reg.drain, k.reg.drain_hi}) {
+        if (!f) continue;
+        e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e != cudaSuccess) return e;
     }
     done = want;
@@ -146,15 +126,17 @@ int device_sm_count() {
 }
 
 // The scan and persistent kernels of a plan (queue or register local solver) and their
-// shared memory.
+// shared memory. Register plans asking for more than kRegBlocks CTAs per SM get the
+// high-occupancy build of the persistent kernel.
 static void (*drain_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
-    return p.local_solver == IWPP_SOLVER_REGISTER ? k.drain_reg : k.drain;
+    if (p.local_solver != IWPP_SOLVER_REGISTER) return k.drain;
+    return p.blocks_per_sm > kRegBlocks ? k.reg.drain_hi : k.reg.drain;
 }
 static void (*scan_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
-    return p.local_solver == IWPP_SOLVER_REGISTER ? k.scan_reg : k.scan;
+    return p.local_solver == IWPP_SOLVER_REGISTER ? k.reg.scan : k.scan;
 }
 static size_t drain_smem(const iwpp_plan &p, const KernelSet &k) {
-    return p.local_solver == IWPP_SOLVER_REGISTER ? k.smem_reg((uint32_t)p.smem_queue_cap)
+    return p.local_solver == IWPP_SOLVER_REGISTER ? k.reg.smem((uint32_t)p.smem_queue_cap)
                                                   : k.smem((uint32_t)p.smem_queue_cap);
 }
 
@@ -532,22 +514,6 @@ extern "C" int iwpp_sync_status(const void *workspace, void *stream) {
     return (int)st;
 }
 
-#if IWPP_TRACE
-// Measurement builds only: copy out and reset the visit trace of the register solver
-// (hist: uint32[16384] visits started per 10 us; returns the longest chain of tile hops).
-extern "C" IWPP_API int iwpp_trace_read(unsigned int *hist_host) {
-    unsigned int mg = 0;
-    cudaMemcpyFromSymbol(&mg, iwpp::g_trace_maxgen, sizeof mg);
-    if (hist_host) cudaMemcpyFromSymbol(hist_host, iwpp::g_trace_hist, sizeof(unsigned int) * iwpp::kTraceBins);
-    static unsigned int zeros[iwpp::kTraceBins];
-    cudaMemcpyToSymbol(iwpp::g_trace_hist, zeros, sizeof zeros);
-    const unsigned int z = 0;
-    cudaMemcpyToSymbol(iwpp::g_trace_maxgen, &z, sizeof z);
-    const unsigned long long big = ~0ull;
-    cudaMemcpyToSymbol(iwpp::g_trace_t0, &big, sizeof big);
-    return (int)mg;
-}
-#endif
 
 extern "C" int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[6]) {
     if (!workspace || !out) return IWPP_ERR_ARG;

@@ -1062,7 +1062,7 @@ __device__ __forceinline__ void queue_warp(const EngineArgs &a, bool want, uint3
     if (want) a.queue[(base + __popc(bal & ((1u << lane) - 1u))) % a.ntiles] = t;
 }
 
-__global__ void __launch_bounds__(256) compact_kernel(EngineArgs a) {
+static __global__ void __launch_bounds__(256) compact_kernel(EngineArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t nround = (a.ntiles + 31) / 32 * 32;
@@ -1078,7 +1078,7 @@ __global__ void __launch_bounds__(256) compact_kernel(EngineArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) finalize_queue_kernel(EngineArgs a) {
+static __global__ void __launch_bounds__(256) finalize_queue_kernel(EngineArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t nround = (a.ntiles + 31) / 32 * 32;
@@ -1100,7 +1100,7 @@ struct DescChunk {
     ImageView v[kDescChunk];
     int first, count;
 };
-__global__ void upload_descs_kernel(ImageView *table, DescChunk c) {
+static __global__ void upload_descs_kernel(ImageView *table, DescChunk c) {
     const int i = threadIdx.x;
     if (i < c.count) table[c.first + i] = c.v[i];
 }

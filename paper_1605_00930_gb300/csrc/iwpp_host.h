@@ -8,6 +8,22 @@
 #include "../../include/iwpp.h"
 
 namespace iwpp {
+struct EngineArgs;
+
+// Kernels of the register local solver for one tile shape and image kind (v = 0..3:
+// bit 0 u16, bit 1 8-connectivity; v = 4: mixed batch). All null when the shape has none.
+// drain_hi is the same persistent kernel compiled for kRegHiBlocks CTAs per SM (fewer
+// registers per thread, more warps to hide latency); plans that ask for more than
+// kRegBlocks CTAs per SM use it.
+struct RegKernelSet {
+    void (*scan)(EngineArgs);
+    void (*drain)(EngineArgs);
+    void (*drain_hi)(EngineArgs);
+    size_t (*smem)(uint32_t);
+};
+constexpr int kRegBlocks = 4, kRegHiBlocks = 6;
+RegKernelSet reg_kernel_set(int th, int tw, int v);
+
 int shape_index(int th, int tw);
 bool plan_valid(const iwpp_plan &p);
 void default_plan(iwpp_plan *p);

@@ -550,8 +550,8 @@ __device__ inline void flush_phases(const EngineArgs &a, const unsigned long lon
 #endif
 }
 
-template <typename T, int CONN, int TH>
-__global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_reg_kernel(EngineArgs a) {
+template <typename T, int CONN, int TH, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) drain_reg_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, TH>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -599,8 +599,8 @@ __global__ void __launch_bounds__(kThreads) scan_reg_mixed_kernel(EngineArgs a) 
 }
 
 // Batch of images of mixed pixel types and connectivities: dispatch on the image's kind.
-template <int TH>
-__global__ void __launch_bounds__(kThreads, IWPP_DRAIN_MINB) drain_reg_mixed_kernel(EngineArgs a) {
+template <int TH, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) drain_reg_mixed_kernel(EngineArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *wsmem = smem_raw + warp * RegTile<uint16_t, 8, TH>::smem_per_warp(0);

@@ -55,7 +55,7 @@ static int graph_create(const iwpp_image *imgs, int n, const iwpp_plan *plan, co
 // Times candidate plans on the batch itself and keeps the fastest. Markers are backed up
 // before and restored before every trial and at the end, so the caller's images are
 // unchanged. Coordinate descent: local solver with its tile shape, then sweep count, then
-// (queue solver only) shared queue capacity.
+// (register solver) CTAs per SM or (queue solver) shared queue capacity.
 struct Tuner {
     const iwpp_image *imgs;
     int n;
@@ -234,6 +234,12 @@ int autotune(const iwpp_image *imgs, int n, iwpp_plan *plan, int reps, const cha
         iwpp_plan c = base;
         c.sweeps = sw;
         consider(c);
+    }
+    base = best;
+    if (base.local_solver == IWPP_SOLVER_REGISTER) {   // occupancy: the high-occupancy build
+        iwpp_plan c = base;
+        c.blocks_per_sm = kRegHiBlocks;
+        if (c.blocks_per_sm != base.blocks_per_sm) consider(c);
     }
     base = best;
     for (int qc : {128, 256, 512, 1024, 2048}) {

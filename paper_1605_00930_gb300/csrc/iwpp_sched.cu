@@ -59,13 +59,120 @@ __device__ __forceinline__ int find_image(const SchedImage *tab, int n, uint32_t
     return lo;
 }
 
-// ---- features: one CTA of 256 threads per block; 4 threads per block row ------------------
+// ---- features: one warp per block; lane c holds columns 2c and 2c + 1 of every row ------------
+// Exact integer sums per lane (8-bit packed histogram counters: at most 128 pixels per lane),
+// warp reductions, then lane 0 converts. Rows are read four at a time so that several loads
+// are in flight per warp; the edge test of a row needs the next row's mask, so it lags by one.
+struct FeatAcc {
+    uint32_t h03 = 0, h47 = 0;   // histogram bins, 8 bits each
+    uint32_t seeds = 0, edges = 0, sI = 0, sJ = 0, sD = 0, n = 0;
+    unsigned long long sI2 = 0, sJ2 = 0;
+};
+
+__device__ __forceinline__ void feat_pixel(FeatAcc &a, uint32_t i, uint32_t j, bool u16) {
+    const uint32_t d = i > j ? i - j : 0u;
+    const uint32_t d8 = u16 ? d >> 8 : d;
+    const uint32_t bin = d8 == 0 ? 0u : min(7u, 32u - (uint32_t)__clz(d8));
+    const uint32_t inc = 1u << (8 * (bin & 3));
+    if (bin < 4) a.h03 += inc; else a.h47 += inc;
+    a.seeds += (i == j && j > 0);
+    a.sI += i;
+    a.sJ += j;
+    a.sD += d;
+    a.sI2 += (unsigned long long)i * i;
+    a.sJ2 += (unsigned long long)j * j;
+    a.n++;
+}
+
+// Pixels (y, x) and (y, x + 1) of plane p (flipped), loaded with clamped addresses; the
+// caller masks the ones outside the block.
+__device__ __forceinline__ void feat_load(const SchedImage &im, const uint8_t *p, int y, int x, uint32_t &e,
+                                          uint32_t &o) {
+    const size_t row = (size_t)y * im.W;
+    const int xe = min(x, im.W - 1), xo = min(x + 1, im.W - 1);
+    if (im.u16) {
+        const uint16_t *q = reinterpret_cast<const uint16_t *>(p) + row;
+        e = q[xe];
+        o = q[xo];
+    } else {
+        e = p[row + xe];
+        o = p[row + xo];
+    }
+    e ^= im.flip;
+    o ^= im.flip;
+}
+
+// Word w (0..3) of a 16-byte chunk, pixel q of the word (4 u8 or 2 u16 per word).
+template <bool U16>
+__device__ __forceinline__ uint32_t px_of(uint32_t w, int q) {
+    return U16 ? (w >> (16 * q)) & 0xFFFFu : (w >> (8 * q)) & 0xFFu;
+}
+
+// A whole 64 x 64 block inside the image whose rows start on 16-byte boundaries: each lane
+// reads 16 bytes of a row (PX pixels); LPR lanes cover a row, RPG rows per load, and the
+// next row group is prefetched while this one is processed. The pixel below a lane's
+// pixels is LPR lanes further (or, for the group's last row, the first row of the next
+// group, one shuffle away); the pixel right of its last one is the next lane's first.
+template <bool U16>
+__device__ __forceinline__ void feat_block_vec(const SchedImage &im, int y0, int x0, uint32_t thr, int lane,
+                                               FeatAcc &a) {
+    constexpr int PX = U16 ? 8 : 16, LPR = 64 / PX, RPG = 32 / LPR, NK = 64 / RPG, PPW = PX / 4;
+    const int g = lane / LPR, sgm = lane % LPR;
+    const size_t pitch = (size_t)im.W * (U16 ? 2 : 1);
+    const uint8_t *baseI = im.I + (size_t)y0 * pitch + (size_t)x0 * (U16 ? 2 : 1) + (size_t)sgm * 16;
+    const uint8_t *baseJ = im.J + (size_t)y0 * pitch + (size_t)x0 * (U16 ? 2 : 1) + (size_t)sgm * 16;
+    const uint32_t f = im.flip | (im.flip << 16);
+    const uint32_t fw = U16 ? f : (im.flip * 0x01010101u);
+    auto ld = [&](const uint8_t *b, int k) {
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(b + (size_t)(k * RPG + g) * pitch));
+        v.x ^= fw; v.y ^= fw; v.z ^= fw; v.w ^= fw;
+        return v;
+    };
+    uint4 I = ld(baseI, 0), J = ld(baseJ, 0);
+    for (int k = 0; k < NK; k++) {
+        uint4 In = I, Jn = J;
+        if (k + 1 < NK) {
+            In = ld(baseI, k + 1);
+            Jn = ld(baseJ, k + 1);
+        }
+        const uint32_t iw[4] = {I.x, I.y, I.z, I.w}, jw[4] = {J.x, J.y, J.z, J.w};
+        // the row below: next lane group in this load, or the next group's first row
+        uint32_t dw[4];
+        const uint32_t nw4[4] = {In.x, In.y, In.z, In.w};
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            const uint32_t below = __shfl_down_sync(0xffffffffu, iw[w], LPR);
+            const uint32_t wrap = __shfl_sync(0xffffffffu, nw4[w], sgm);   // group 0 of the next load
+            dw[w] = g < RPG - 1 ? below : wrap;
+        }
+        const bool has_down = !(g == RPG - 1 && k == NK - 1);
+        const uint32_t right = __shfl_down_sync(0xffffffffu, iw[0], 1);   // next lane's first word
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+#pragma unroll
+            for (int q = 0; q < PPW; q++) {
+                const uint32_t i = px_of<U16>(iw[w], q), j = px_of<U16>(jw[w], q);
+                feat_pixel(a, i, j, U16);
+                uint32_t r;
+                if (q + 1 < PPW) r = px_of<U16>(iw[w], q + 1);
+                else if (w < 3) r = px_of<U16>(iw[w + 1], 0);
+                else r = px_of<U16>(right, 0);
+                const bool has_right = !(w == 3 && q == PPW - 1 && sgm == LPR - 1);
+                const uint32_t gx = has_right ? (uint32_t)abs((int)r - (int)i) : 0u;
+                const uint32_t gy = has_down ? (uint32_t)abs((int)px_of<U16>(dw[w], q) - (int)i) : 0u;
+                a.edges += (gx + gy > thr);
+            }
+        }
+        I = In;
+        J = Jn;
+    }
+}
+
 __global__ void __launch_bounds__(256) features_kernel(const SchedImage *tab, int nimg, uint32_t nblocks,
                                                        float *out) {
-    __shared__ unsigned long long acc[16];   // 8 hist, seeds, edges, sI, sI2, sJ, sJ2, sD, n
-    for (uint32_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
-        if (threadIdx.x < 16) acc[threadIdx.x] = 0;
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nblocks; b += nw) {
         const int k = find_image(tab, nimg, b, [](const SchedImage &s) { return s.block_base; });
         const SchedImage im = tab[k];
         const uint32_t lb = b - im.block_base;
@@ -73,56 +180,86 @@ __global__ void __launch_bounds__(256) features_kernel(const SchedImage *tab, in
         const int ye = min(im.H, y0 + kBlk), xe = min(im.W, x0 + kBlk);
         const uint32_t M = im.u16 ? 0xFFFFu : 0xFFu;
         const uint32_t thr = 16u * (M / 255u);
-        unsigned long long hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        unsigned long long seeds = 0, edges = 0, sI = 0, sI2 = 0, sJ = 0, sJ2 = 0, sD = 0, n = 0;
-        const int r = y0 + (int)(threadIdx.x >> 2), cb = x0 + 16 * (int)(threadIdx.x & 3);
-        auto ld = [&](const uint8_t *p, int y, int x) -> uint32_t {
-            const size_t e = (size_t)y * im.W + x;
-            const uint32_t v = im.u16 ? reinterpret_cast<const uint16_t *>(p)[e] : p[e];
-            return v ^ im.flip;
+        const bool u16 = im.u16 != 0;
+        FeatAcc a;
+        const size_t pitch = (size_t)im.W * (u16 ? 2 : 1);
+        if (x0 + kBlk <= im.W && y0 + kBlk <= im.H && pitch % 16 == 0 &&
+            ((uintptr_t)im.I & 15) == 0 && ((uintptr_t)im.J & 15) == 0) {
+            if (u16) feat_block_vec<true>(im, y0, x0, thr, lane, a);
+            else feat_block_vec<false>(im, y0, x0, thr, lane, a);
+        } else {
+        const int c = x0 + 2 * lane;
+        const bool ine = c < xe, ino = c + 1 < xe, inr = c + 2 < xe;   // this pair, and the next lane's
+        uint32_t pe = 0, po = 0;   // mask of the previous row (edges lag by one row)
+        auto edges_of = [&](uint32_t ie, uint32_t io, uint32_t de, uint32_t dn, bool has_down) {
+            // ie / io: a row's pair; de / dn: the pair below (ignored when !has_down)
+            const uint32_t nxt = __shfl_down_sync(0xffffffffu, ie, 1);   // column 2c + 2
+            const uint32_t gxe = ino ? (uint32_t)abs((int)io - (int)ie) : 0u;
+            const uint32_t gxo = inr ? (uint32_t)abs((int)nxt - (int)io) : 0u;
+            const uint32_t gye = has_down ? (uint32_t)abs((int)de - (int)ie) : 0u;
+            const uint32_t gyo = has_down ? (uint32_t)abs((int)dn - (int)io) : 0u;
+            if (ine) a.edges += (gxe + gye > thr);
+            if (ino) a.edges += (gxo + gyo > thr);
         };
-        if (r < ye) {
-            for (int x = cb; x < min(cb + 16, xe); x++) {
-                const uint32_t i = ld(im.I, r, x), j = ld(im.J, r, x);
-                const uint32_t d = i > j ? i - j : 0u;
-                const uint32_t d8 = im.u16 ? d >> 8 : d;
-                hist[d8 == 0 ? 0 : min(7, 32 - __clz(d8))]++;
-                seeds += (i == j && j > 0);
-                const uint32_t gx = x + 1 < xe ? (uint32_t)abs((int)ld(im.I, r, x + 1) - (int)i) : 0u;
-                const uint32_t gy = r + 1 < ye ? (uint32_t)abs((int)ld(im.I, r + 1, x) - (int)i) : 0u;
-                edges += (gx + gy > thr);
-                sI += i;
-                sI2 += (unsigned long long)i * i;
-                sJ += j;
-                sJ2 += (unsigned long long)j * j;
-                sD += d;
-                n++;
+        for (int y = y0; y < ye; y += 4) {
+            uint32_t Ie[4], Io[4], Je[4], Jo[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int yy = min(y + q, ye - 1);
+                feat_load(im, im.I, yy, c, Ie[q], Io[q]);
+                feat_load(im, im.J, yy, c, Je[q], Jo[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (y + q >= ye) break;   // warp-uniform
+                if (ine) feat_pixel(a, Ie[q], Je[q], u16);
+                if (ino) feat_pixel(a, Io[q], Jo[q], u16);
+                if (y + q > y0) edges_of(pe, po, Ie[q], Io[q], true);
+                pe = Ie[q];
+                po = Io[q];
             }
         }
-        unsigned long long v[16] = {hist[0], hist[1], hist[2], hist[3], hist[4], hist[5], hist[6], hist[7],
-                                    seeds, edges, sI, sI2, sJ, sJ2, sD, n};
+        edges_of(pe, po, 0u, 0u, false);   // the block's last row has no row below
+        }
+
+        uint32_t v[16];
 #pragma unroll
-        for (int q = 0; q < 16; q++) {
-            unsigned long long x = v[q];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if ((threadIdx.x & 31) == 0 && x) atomicAdd(&acc[q], x);
+        for (int q = 0; q < 4; q++) {
+            v[q] = __reduce_add_sync(0xffffffffu, (a.h03 >> (8 * q)) & 0xFFu);
+            v[4 + q] = __reduce_add_sync(0xffffffffu, (a.h47 >> (8 * q)) & 0xFFu);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double N = (double)acc[15], Mv = (double)M;
-            float *f = out + (size_t)b * kNF;
-            for (int q = 0; q < 8; q++) f[q] = (float)((double)acc[q] / N);
-            f[8] = (float)((double)acc[8] / N);
-            f[9] = (float)((double)acc[9] / N);
-            const double mI = (double)acc[10] / N, mJ = (double)acc[12] / N;
-            f[10] = (float)(mI / Mv);
-            f[11] = (float)(sqrt(fmax(0.0, (double)acc[11] / N - mI * mI)) / Mv);
-            f[12] = (float)(mJ / Mv);
-            f[13] = (float)(sqrt(fmax(0.0, (double)acc[13] / N - mJ * mJ)) / Mv);
-            f[14] = (float)((double)acc[14] / N / Mv);
-            f[15] = (float)(log2(N) / 12.0);
+        v[8] = __reduce_add_sync(0xffffffffu, a.seeds);
+        v[9] = __reduce_add_sync(0xffffffffu, a.edges);
+        v[10] = __reduce_add_sync(0xffffffffu, a.sI);   // < 2^32: 4096 pixels x 65535
+        v[12] = __reduce_add_sync(0xffffffffu, a.sJ);
+        v[14] = __reduce_add_sync(0xffffffffu, a.sD);
+        v[15] = __reduce_add_sync(0xffffffffu, a.n);
+        unsigned long long sI2 = a.sI2, sJ2 = a.sJ2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the sums
+            sI2 += __shfl_xor_sync(0xffffffffu, sI2, o);
+            sJ2 += __shfl_xor_sync(0xffffffffu, sJ2, o);
         }
-        __syncthreads();
+        // Conversion in FP32 (FP64 is slow on this part) from exact integers: the variance
+        // numerator N * sum(x^2) - sum(x)^2 is exact in 64 bits (N <= 4096, x <= 65535),
+        // so no cancellation; every feature is within a few float ulps of the exact value.
+        if (lane < kNF) {
+            const uint32_t N = v[15];
+            const float fN = (float)N, NM = (float)N * (float)M;
+            const unsigned long long vI = (unsigned long long)N * sI2 - (unsigned long long)v[10] * v[10];
+            const unsigned long long vJ = (unsigned long long)N * sJ2 - (unsigned long long)v[12] * v[12];
+            float r;
+            switch (lane) {
+                case 10: r = (float)v[10] / NM; break;
+                case 11: r = sqrtf((float)vI) / NM; break;
+                case 12: r = (float)v[12] / NM; break;
+                case 13: r = sqrtf((float)vJ) / NM; break;
+                case 14: r = (float)v[14] / NM; break;
+                case 15: r = log2f(fN) / 12.f; break;
+                default: r = (float)v[lane] / fN; break;   // histogram, seeds, edges
+            }
+            out[(size_t)b * kNF + lane] = r;
+        }
     }
 }
 
@@ -312,9 +449,22 @@ __global__ void sched_scan_kernel(uint32_t *hist) {   // exclusive scan, one blo
     hist[i] = s[i] - hist[i];
 }
 
+// Scatter tiles to their bucket's next slots. Lanes with the same key share one atomic
+// (many tiles fall into few buckets), and keep their lane order inside the group.
 __global__ void sched_scatter_kernel(uint32_t ntiles, const uint16_t *key, uint32_t *cursor, uint32_t *order) {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
-        order[atomicAdd(cursor + key[t], 1u)] = t;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;   // a multiple of 32: t0 stays warp-uniform
+    for (uint32_t t0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; t0 < ntiles; t0 += stride) {
+        const uint32_t t = t0 + lane;
+        const bool valid = t < ntiles;
+        const uint32_t k = valid ? key[t] : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xffffffffu, k);
+        const int leader = __ffs(peers) - 1;
+        uint32_t slot = 0;
+        if (lane == leader && valid) slot = atomicAdd(cursor + k, (uint32_t)__popc(peers));
+        slot = __shfl_sync(0xffffffffu, slot, leader);
+        if (valid) order[slot + __popc(peers & ((1u << lane) - 1u))] = t;
+    }
 }
 
 // Per-tile work (pops or passes, cycles) summed into feature blocks: out[b] = pops or passes,
@@ -420,7 +570,7 @@ static int schedule_impl(const iwpp_image *imgs, int n, const iwpp_plan *plan_in
     float *feats = feats_out ? feats_out : reinterpret_cast<float *>(base + L.feats);
     float *preds = reinterpret_cast<float *>(base + L.preds);
     if (upload_table(imgs, n, p, bb, tb, table, stream) != IWPP_OK) return IWPP_ERR_CUDA;
-    if (phases & 1) features_kernel<<<grid_for(L.nblocks, 1, 16), 256, 0, stream>>>(table, n, L.nblocks, feats);
+    if (phases & 1) features_kernel<<<grid_for(L.nblocks, 8, 8), 256, 0, stream>>>(table, n, L.nblocks, feats);
     if (phases & 2) {
         if (!params) return IWPP_ERR_ARG;
         mlp_forward_kernel<<<grid_for(L.nblocks, 256, 4), 256, 0, stream>>>(params, feats, L.nblocks, preds);

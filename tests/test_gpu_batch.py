@@ -58,23 +58,26 @@ def _check(oracle_lib, cases, outs):
                                  f"{len(bad)} mismatches, first at {tuple(bad[0])}")
 
 
-@pytest.mark.parametrize("tile,solver", [((32, 32), 0), ((32, 64), 0), ((64, 64), 0), ((16, 32), 0),
-                                         ((16, 64), 0), ((16, 64), 1)])
-def test_mixed_batch_static(iw, oracle_lib, tile, solver):
+@pytest.mark.parametrize("tile,solver,bps", [((32, 32), 0, 0), ((32, 64), 0, 0), ((64, 64), 0, 0),
+                                             ((16, 32), 0, 0), ((16, 64), 0, 0), ((16, 64), 1, 0),
+                                             ((16, 64), 1, 6)])
+def test_mixed_batch_static(iw, oracle_lib, tile, solver, bps):
     cases = _mixed_cases(5, 24)
     p = iw.iwpp_default_plan()
     p.tile_h, p.tile_w = tile
     p.local_solver = solver
+    p.blocks_per_sm = bps
     outs, _, _ = _run_batch(iw, cases, p)
     _check(oracle_lib, cases, outs)
 
 
-@pytest.mark.parametrize("solver", [0, 1])
-def test_uniform_batch_each_kind(iw, oracle_lib, solver):
+@pytest.mark.parametrize("solver,bps", [(0, 0), (1, 0), (1, 6)])
+def test_uniform_batch_each_kind(iw, oracle_lib, solver, bps):
     """Batches whose images share pixel type and connectivity use the specialised kernels."""
     p = iw.iwpp_default_plan()
     p.tile_h, p.tile_w = (32, 32) if solver == 0 else (16, 64)
     p.local_solver = solver
+    p.blocks_per_sm = bps
     for k, (dtype, conn) in enumerate([(np.uint8, 4), (np.uint16, 4), (np.uint8, 8), (np.uint16, 8)]):
         cases = []
         for i, (H, W) in enumerate([(77, 301), (256, 64), (19, 1000)]):

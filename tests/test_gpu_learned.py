@@ -52,6 +52,22 @@ def test_features_match_oracle(iw):
     np.testing.assert_allclose(got, exp, rtol=1e-6, atol=1e-7)
 
 
+@pytest.mark.parametrize("shape", [(128, 192), (130, 256), (64, 80), (200, 320)])
+@pytest.mark.parametrize("is16", [False, True])
+def test_features_vector_path_matches_oracle(iw, shape, is16):
+    """Whole 64 x 64 blocks with 16-byte row pitch take the vectorised path; ragged edge
+    blocks (and rows that are not 16-byte multiples) the scalar one. Both are exact."""
+    from paper_1605_00930_gb300 import learned
+    rng = synth.rng_for(97, shape[0] * 1000 + shape[1] + is16)
+    f = synth.blob_field_u8(*shape, 12, rng)
+    mask = synth.to_u16(f) if is16 else f
+    cases = [synth.Case(synth.hdome_marker(mask, 20 * (257 if is16 else 1)), mask, 8, "dilate"),
+             synth.Case(synth.fillholes_marker(mask), mask, 8, "erode")]
+    got = learned.features(_items(cases)).cpu().numpy()
+    exp = ofeat.batch_features(cases)
+    np.testing.assert_allclose(got, exp, rtol=1e-6, atol=1e-7)
+
+
 def test_mlp_forward_matches_oracle(iw):
     rng = np.random.default_rng(2)
     p = omlp.init_params(4).astype(np.float32)

@@ -127,7 +127,7 @@ def test_plans_tissue(iw, oracle_lib, tile, sweeps, qcap):
 
 
 @pytest.mark.parametrize("sweeps", [0, 1, 3])
-@pytest.mark.parametrize("bps", [0, 1])
+@pytest.mark.parametrize("bps", [0, 1, 5, 6])
 def test_plans_tissue_register(iw, oracle_lib, sweeps, bps):
     c = synth.tissue_case(301, 517, nblobs=30)
     p = _plan(iw, sweeps=sweeps, blocks_per_sm=bps, **SOLVERS["register"])

@@ -168,7 +168,7 @@ bool plan_valid(const iwpp_plan &p) {
     if (p.blocks_per_sm < 0 || p.blocks_per_sm > 32) return false;
     if (p.watchdog_ns < 0) return false;
     if (p.local_solver != IWPP_SOLVER_QUEUE && p.local_solver != IWPP_SOLVER_REGISTER) return false;
-    if (p.local_solver == IWPP_SOLVER_REGISTER && (p.tile_w != 64 || p.tile_h > 16)) return false;
+    if (p.local_solver == IWPP_SOLVER_REGISTER && !reg_kernel_set(p.tile_h, p.tile_w, 0).drain) return false;
     if (p.reserved != 0) return false;
     return true;
 }

@@ -37,7 +37,7 @@ __device__ __forceinline__ uint32_t right_of(uint32_t v, uint32_t n) { return __
 
 template <typename T, int CONN, int TH>
 struct RegTile {
-    static_assert(TH >= 2 && TH <= 30, "tile rows (one lane per halo row)");
+    static_assert(TH >= 2 && TH <= 32, "tile rows");
     static constexpr int TW = 64;
     struct Smem {
         uint32_t *hxJ;          // 2 x (TH + 2): [0..TH+1] left halo column << 16, [TH+2..] right halo column
@@ -103,8 +103,8 @@ struct RegTile {
             it = ld_pair(im, im.I, y0 - 1, gx, false);
             ib = ld_pair(im, im.I, y0 + TH, gx, false);
         }
-        if (lane < TH + 2) {
-            const int gy = y0 + lane - 1;
+        for (int hr = lane; hr < TH + 2; hr += 32) {
+            const int gy = y0 + hr - 1;
             const bool rowin = gy >= 0 && gy < im.H;
             const bool lin = rowin && x0 > 0, rin = rowin && x0 + TW < im.W;
             const size_t row = (size_t)min(max(gy, 0), im.H - 1) * im.W;
@@ -115,11 +115,11 @@ struct RegTile {
                 li = ld1(im.I, el, false);
                 ri = ld1(im.I, er, false);
             }
-            s.hxJ[lane] = lin ? (lj ^ im.flip) << 16 : 0u;
-            s.hxJ[TH + 2 + lane] = rin ? rj ^ im.flip : 0u;
+            s.hxJ[hr] = lin ? (lj ^ im.flip) << 16 : 0u;
+            s.hxJ[TH + 2 + hr] = rin ? rj ^ im.flip : 0u;
             if (withI) {
-                s.hlI[lane] = lin ? li ^ im.flip : 0u;
-                s.hrI[lane] = rin ? ri ^ im.flip : 0u;
+                s.hlI[hr] = lin ? li ^ im.flip : 0u;
+                s.hrI[hr] = rin ? ri ^ im.flip : 0u;
             }
         }
         __syncwarp();
@@ -506,14 +506,22 @@ __device__ void visit_tile_reg(const EngineArgs &a, const ImageView &im, uint32_
             if (!more) break;
         }
         st.visits++;
-        if (rows) RT::store(im, y0, x0, J, rows, lane);
-        IWPP_RT_MARK(3);
-        RT::notify_scan(s, J, jt, jb, it, ib, lane);
-        IWPP_RT_MARK(4);
-        __threadfence();
-        __syncwarp();
-        IWPP_RT_MARK(5);
-        if (lane < 9 && lane != 4 && s.misc[lane]) {
+        // A round that raised nothing leaves the tile as it was when its last notifications
+        // were sent (the previous visit, or the scan): no neighbour can have gained work.
+        const bool changed = __any_sync(0xffffffffu, rows != 0);
+#if IWPP_COUNT_IDLE_VISITS
+        st.pops += changed ? 0u : 1u;   // measurement builds: rounds that raised nothing
+#endif
+        if (changed) {
+            RT::store(im, y0, x0, J, rows, lane);
+            IWPP_RT_MARK(3);
+            RT::notify_scan(s, J, jt, jb, it, ib, lane);
+            IWPP_RT_MARK(4);
+            __threadfence();
+            __syncwarp();
+            IWPP_RT_MARK(5);
+        }
+        if (changed && lane < 9 && lane != 4 && s.misc[lane]) {
             const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
             if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x) {
                 const uint32_t n = im.tile_base + (uint32_t)(ny * im.tiles_x + nx);

@@ -89,7 +89,13 @@ typedef enum {
  *                      columns per lane) and swept down and up until no pixel
  *                      changes (Algorithm 1's update in Gauss-Seidel order);
  *                      the register solver needs tile_w == 64, tile_h <= 16
- *   reserved           must be 0
+ *   value_levels       0 or 1: the persistent kernel's tile queue is one FIFO;
+ *                      2..16: one queue per value level, and a worker takes
+ *                      its next tile from the highest level that has one (the
+ *                      level of a queued tile is the value the notification
+ *                      that queued it can raise it to; the tile-granular form of
+ *                      Sec. 3.2's heap-ordered propagation). Register solver,
+ *                      single-image calls only
  *   watchdog_ns        the persistent kernel gives up with IWPP_ERR_TIMEOUT
  *                      when a wait for work lasts longer than this
  *                      (0 = default, 10 s)
@@ -101,7 +107,7 @@ typedef struct {
     int32_t smem_queue_cap;
     int32_t blocks_per_sm;
     int32_t local_solver;
-    int32_t reserved;
+    int32_t value_levels;
     int64_t watchdog_ns;
 } iwpp_plan;
 

@@ -169,7 +169,8 @@ bool plan_valid(const iwpp_plan &p) {
     if (p.watchdog_ns < 0) return false;
     if (p.local_solver != IWPP_SOLVER_QUEUE && p.local_solver != IWPP_SOLVER_REGISTER) return false;
     if (p.local_solver == IWPP_SOLVER_REGISTER && !reg_kernel_set(p.tile_h, p.tile_w, 0).drain) return false;
-    if (p.reserved != 0) return false;
+    if (p.value_levels < 0 || p.value_levels > kMaxLevels) return false;
+    if (p.value_levels > 1 && p.local_solver != IWPP_SOLVER_REGISTER) return false;
     return true;
 }
 
@@ -184,7 +185,7 @@ void default_plan(iwpp_plan *p) {
     p->smem_queue_cap = 512;
     p->blocks_per_sm = 0;
     p->local_solver = IWPP_SOLVER_REGISTER;
-    p->reserved = 0;
+    p->value_levels = 0;
     p->watchdog_ns = 0;
 }
 
@@ -227,13 +228,16 @@ static void fill_common(EngineArgs &a, const iwpp_plan &p, uint8_t *base, size_t
     a.watchdog_ns = p.watchdog_ns > 0 ? p.watchdog_ns : 10ll * 1000 * 1000 * 1000;
     a.imgs = nullptr;
     a.nimg = 0;
+    a.nlevels = p.value_levels > 1 ? (uint32_t)p.value_levels : 1u;
+    a.lvl = nullptr;
 }
 
 // ---- single image ------------------------------------------------------------------------------
-// Workspace: header (256 B) | tile states | tile-queue slots | per-warp overflow queues.
+// Workspace: header (256 B) | tile states | level counters | tile-queue slots (one ring per
+// value level) | per-warp overflow queues.
 struct Layout {
-    size_t state, queue, ovf, total;
-    uint32_t ntiles, ovcap;
+    size_t state, lvl, queue, ovf, total;
+    uint32_t ntiles, ovcap, nlevels;
     int grid;
 };
 
@@ -245,9 +249,11 @@ static bool make_layout(int64_t H, int64_t W, int v, const iwpp_plan &p, Layout 
     L.grid = drain_grid(p, v, L.ntiles);
     if (L.grid <= 0) return false;
     L.ovcap = (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap);
+    L.nlevels = p.value_levels > 1 ? (uint32_t)p.value_levels : 1u;
     L.state = 256;
-    L.queue = L.state + align256((size_t)L.ntiles * 4);
-    L.ovf = L.queue + align256((size_t)L.ntiles * 4);
+    L.lvl = L.state + align256((size_t)L.ntiles * 4);
+    L.queue = L.lvl + align256(sizeof(LevelCtr) * kMaxLevels);
+    L.ovf = L.queue + align256((size_t)L.ntiles * 4 * L.nlevels);
     L.total = L.ovf + align256((size_t)L.grid * kWarpsPerCta * 2 * L.ovcap * sizeof(uint16_t) + 16);
     return true;
 }
@@ -276,6 +282,7 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
     EngineArgs a;
     fill_common(a, p, base, L.state, L.queue, L.ovf, L.ntiles, L.ovcap);
     a.img0 = make_view(marker, mask, H, W, conn, op, dtype, p, 0);
+    a.lvl = reinterpret_cast<LevelCtr *>(base + L.lvl);
 
     const int shape = shape_index(p.tile_h, p.tile_w);
     const KernelSet &k = kernels(shape, v);
@@ -283,8 +290,9 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
     if (ensure_smem_attr(shape, v, smem) != cudaSuccess) return IWPP_ERR_CUDA;
 
     if (phases & kPhaseScan) {
-        if (cudaMemsetAsync(base, 0, L.queue, stream) != cudaSuccess) return IWPP_ERR_CUDA;  // header + states
-        if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4, stream) != cudaSuccess)
+        // header, tile states, level counters
+        if (cudaMemsetAsync(base, 0, L.queue, stream) != cudaSuccess) return IWPP_ERR_CUDA;
+        if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4 * L.nlevels, stream) != cudaSuccess)
             return IWPP_ERR_CUDA;
         const int sms = device_sm_count();
         const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -380,7 +388,7 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
                       cudaStream_t stream) {
     iwpp_plan p;
     if (plan_in) p = *plan_in; else default_plan(&p);
-    if (!plan_valid(p)) return IWPP_ERR_ARG;
+    if (!plan_valid(p) || p.value_levels > 1) return IWPP_ERR_ARG;   // batches: one FIFO
     if (!imgs || n < 1) return IWPP_ERR_ARG;
     for (int i = 0; i < n; i++)
         if (check_image(imgs[i]) != IWPP_OK) return IWPP_ERR_ARG;

@@ -100,6 +100,14 @@ struct ImageView {
     uint32_t pad;
 };
 
+// Counters of one value level of the tile queue (value-ordered mode).
+struct LevelCtr {
+    unsigned long long head, tail;   // pop / push tickets
+    int avail;                       // entries published and not yet claimed
+    uint32_t pad[3];
+};
+constexpr int kMaxLevels = 16;
+
 // Everything the kernels of one call share. A single-image call uses img0; a batch
 // call reads its images from the device table `imgs` (sorted by tile_base).
 struct EngineArgs {
@@ -120,6 +128,8 @@ struct EngineArgs {
     uint32_t *tile_work;         // optional per-tile counters: [t] pops, [ntiles + t] SM cycles
     int defer_push;              // scan kernel marks tiles PENDING; the compact kernel queues them
     long long watchdog_ns;
+    uint32_t nlevels;            // 1: one FIFO ring; >1: one ring per value level (queue + L * ntiles)
+    LevelCtr *lvl;               // nlevels counters (value-ordered mode)
 };
 
 // ---- small device helpers ------------------------------------------------------------------
@@ -161,18 +171,92 @@ __device__ inline bool push_tile(const EngineArgs &a, uint32_t t) {
     return true;
 }
 
+// ---- value-ordered tile queue (Sec. 3.2's heap-based propagation, at tile granularity) ---
+// One ticketed ring per value level. A push publishes its entry and then counts it in
+// `avail`; a pop first claims one published entry of the highest level that has one (an
+// atomic decrement that it undoes if it lost the race for the last entry), then takes a
+// ticket: the push holding that ticket has published or is about to, so the wait is short
+// and a popper never waits on an empty level. A tile is queued at most once, at the level
+// of the notification that made it PENDING.
+__device__ inline bool push_tile_level(const EngineArgs &a, uint32_t t, uint32_t level) {
+    LevelCtr *c = a.lvl + level;
+    const unsigned long long ticket = atomicAdd(&c->tail, 1ull);
+    uint32_t *slot = a.queue + (size_t)level * a.ntiles + (ticket % a.ntiles);
+    const unsigned long long t0 = globaltimer_ns();
+    while (atomicCAS(slot, kEmptySlot, t) != kEmptySlot) {
+        if (globaltimer_ns() - t0 > (unsigned long long)a.watchdog_ns) {
+            set_status(a.hdr, kErrTimeout);
+            return false;
+        }
+        if (fatal(a.hdr)) return false;
+        __nanosleep(32);
+    }
+    atomicAdd(&c->avail, 1);
+    return true;
+}
+
+__device__ inline uint32_t pop_tile_level(const EngineArgs &a) {
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned int backoff = 32;
+    for (;;) {
+        int av[kMaxLevels];
+#pragma unroll
+        for (int l = 0; l < kMaxLevels; l++)
+            av[l] = l < (int)a.nlevels ? *reinterpret_cast<const volatile int *>(&a.lvl[l].avail) : 0;
+        int best = -1;
+#pragma unroll
+        for (int l = 0; l < kMaxLevels; l++)
+            if (av[l] > 0) best = l;
+        if (best >= 0) {
+            LevelCtr *c = a.lvl + best;
+            if (atomicSub(&c->avail, 1) > 0) {
+                const unsigned long long ticket = atomicAdd(&c->head, 1ull);
+                uint32_t *slot = a.queue + (size_t)best * a.ntiles + (ticket % a.ntiles);
+                for (;;) {
+                    const uint32_t v = ld_volatile(slot);
+                    if (v != kEmptySlot && atomicCAS(slot, v, kEmptySlot) == v) return v;
+                    if (fatal(a.hdr)) return kDone;
+                    if (globaltimer_ns() - t0 > (unsigned long long)a.watchdog_ns) {
+                        set_status(a.hdr, kErrTimeout);
+                        return kDone;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            atomicAdd(&c->avail, 1);   // lost the race for the level's last entry
+            continue;
+        }
+        if (ld_volatile(&a.hdr->pending) == 0) return kDone;
+        if (fatal(a.hdr)) return kDone;
+        if (globaltimer_ns() - t0 > (unsigned long long)a.watchdog_ns) {
+            set_status(a.hdr, kErrTimeout);
+            return kDone;
+        }
+        __nanosleep(backoff);
+        if (backoff < IWPP_BACKOFF_MAX) backoff <<= 1;
+    }
+}
+
+// Queue level of a raise to value v (dilation domain) of an image.
+__device__ __forceinline__ uint32_t level_of(const EngineArgs &a, const ImageView &im, uint32_t v) {
+    if (a.nlevels <= 1) return 0;
+    return min((v * a.nlevels) >> ((im.kind & 1u) ? 16 : 8), a.nlevels - 1);
+}
+
 // Tile t has a pixel that a halo pixel can raise: make it PENDING (queue it if idle).
 // The queue entry is written only after the state change has returned (a control
 // dependency on its old value), so a popper always finds the tile PENDING.
-__device__ inline void notify_tile(const EngineArgs &a, uint32_t t) {
+__device__ inline void notify_tile(const EngineArgs &a, uint32_t t, uint32_t level = 0) {
     const uint32_t old = atomicOr(a.state + t, ST_PENDING);
     if ((old & (ST_PENDING | ST_ACTIVE)) == 0) {
         atomicAdd(&a.hdr->pending, 1u);
-        push_tile(a, t);
+        if (a.nlevels > 1) push_tile_level(a, t, level);
+        else push_tile(a, t);
     }
 }
 
 __device__ inline uint32_t pop_tile(const EngineArgs &a) {
+    if (a.nlevels > 1) return pop_tile_level(a);
     const unsigned long long ticket = atomicAdd(&a.hdr->head, 1ull);
     uint32_t *slot = a.queue + (ticket % a.ntiles);
     const unsigned long long t0 = globaltimer_ns();

@@ -303,8 +303,15 @@ struct RegTile {
         return __any_sync(0xffffffffu, any);
     }
 
-    // For every halo pixel: can one step from the tile's own pixels raise it above its
-    // loaded value? Flag the owning neighbour (misc[(dy + 1) * 3 + dx + 1]).
+    // Largest value one step from the tile's own pixels can raise a halo pixel to, per
+    // neighbour (misc[(dy + 1) * 3 + dx + 1]; 0 = no halo pixel of that neighbour can rise
+    // above its loaded value). The value sets the neighbour's queue level.
+    static __device__ __forceinline__ uint32_t raise2(uint32_t cand, uint32_t cur) {
+        // per half: the candidate where it exceeds the current value, else 0; max of halves
+        const uint32_t lo = (cand & 0xFFFFu) > (cur & 0xFFFFu) ? (cand & 0xFFFFu) : 0u;
+        const uint32_t hi = (cand >> 16) > (cur >> 16) ? (cand >> 16) : 0u;
+        return max(lo, hi);
+    }
     static __device__ void notify_scan(const Smem &s, const uint32_t (&J)[TH], uint32_t jt, uint32_t jb,
                                        uint32_t it, uint32_t ib, int lane) {
         if (lane == 0) {
@@ -318,26 +325,63 @@ struct RegTile {
         // top and bottom halo rows: the tile's neighbours only (0 beyond its side columns)
         const uint32_t mt = CONN == 8 ? hmax(J[0], 0u, lane) : J[0];
         const uint32_t mb = CONN == 8 ? hmax(J[TH - 1], 0u, lane) : J[TH - 1];
-        if (max2(min2(it, mt), jt) != jt) s.misc[1] = 1;
-        if (max2(min2(ib, mb), jb) != jb) s.misc[7] = 1;
+        const uint32_t vt = __reduce_max_sync(0xffffffffu, raise2(min2(it, mt), jt));
+        const uint32_t vb = __reduce_max_sync(0xffffffffu, raise2(min2(ib, mb), jb));
+        if (lane == 0) {
+            s.misc[1] = vt;
+            s.misc[7] = vb;
+        }
         __syncwarp();
         // left and right halo columns, one row per lane
-        if (lane < TH) {
-            const int r = lane;
+        uint32_t vl = 0, vr = 0;
+        for (int r = lane; r < TH; r += 32) {
             uint32_t ml = s.col0[r], mr = s.col63[r];
             if (CONN == 8) {
                 if (r > 0) { ml = max(ml, s.col0[r - 1]); mr = max(mr, s.col63[r - 1]); }
                 if (r < TH - 1) { ml = max(ml, s.col0[r + 1]); mr = max(mr, s.col63[r + 1]); }
             }
-            if (min(s.hlI[r + 1], ml) > (s.hxJ[r + 1] >> 16)) s.misc[3] = 1;
-            if (min(s.hrI[r + 1], mr) > s.hxJ[TH + 2 + r + 1]) s.misc[5] = 1;
+            const uint32_t cl = min(s.hlI[r + 1], ml), cr = min(s.hrI[r + 1], mr);
+            if (cl > (s.hxJ[r + 1] >> 16)) vl = max(vl, cl);
+            if (cr > s.hxJ[TH + 2 + r + 1]) vr = max(vr, cr);
         }
-        if (CONN == 8 && lane == 0) {   // corners
-            if (min(s.hlI[0], s.col0[0]) > (s.hxJ[0] >> 16)) s.misc[0] = 1;
-            if (min(s.hlI[TH + 1], s.col0[TH - 1]) > (s.hxJ[TH + 1] >> 16)) s.misc[6] = 1;
-            if (min(s.hrI[0], s.col63[0]) > s.hxJ[TH + 2]) s.misc[2] = 1;
-            if (min(s.hrI[TH + 1], s.col63[TH - 1]) > s.hxJ[2 * TH + 3]) s.misc[8] = 1;
+        vl = __reduce_max_sync(0xffffffffu, vl);
+        vr = __reduce_max_sync(0xffffffffu, vr);
+        if (lane == 0) {
+            s.misc[3] = vl;
+            s.misc[5] = vr;
+            uint32_t c0 = 0, c2 = 0, c6 = 0, c8 = 0;
+            if (CONN == 8) {   // corners
+                const uint32_t a0 = min(s.hlI[0], s.col0[0]), a6 = min(s.hlI[TH + 1], s.col0[TH - 1]);
+                const uint32_t a2 = min(s.hrI[0], s.col63[0]), a8 = min(s.hrI[TH + 1], s.col63[TH - 1]);
+                c0 = a0 > (s.hxJ[0] >> 16) ? a0 : 0u;
+                c6 = a6 > (s.hxJ[TH + 1] >> 16) ? a6 : 0u;
+                c2 = a2 > s.hxJ[TH + 2] ? a2 : 0u;
+                c8 = a8 > s.hxJ[2 * TH + 3] ? a8 : 0u;
+            }
+            s.misc[0] = c0;
+            s.misc[2] = c2;
+            s.misc[6] = c6;
+            s.misc[8] = c8;
         }
+    }
+
+    // Largest value any pixel of the tile can still be raised to (0: none can rise).
+    static __device__ __forceinline__ uint32_t raise_max(const uint32_t *hx, const uint32_t (&J)[TH],
+                                                         const uint32_t (&I)[TH], uint32_t jt, uint32_t jb,
+                                                         int lane) {
+        uint32_t best = 0;
+        uint32_t prev = CONN == 8 ? hmax(jt, hx[0], lane) : jt;
+        uint32_t cur = hmax(J[0], hx[1], lane);
+#pragma unroll
+        for (int r = 0; r < TH; r++) {
+            const uint32_t nxt = r + 1 < TH ? J[r + 1 < TH ? r + 1 : r] : jb;
+            const uint32_t nxtH = hmax(nxt, hx[r + 2], lane);
+            const uint32_t m = max2(cur, max2(prev, CONN == 8 ? nxtH : nxt));
+            best = max(best, raise2(min2(I[r], m), J[r]));
+            prev = CONN == 8 ? cur : J[r];
+            cur = nxtH;
+        }
+        return __reduce_max_sync(0xffffffffu, best);
     }
 
     // Store this lane's pairs of the rows it changed (rows below the image never change).
@@ -420,7 +464,7 @@ __device__ void scan_tile_reg(const EngineArgs &a, const ImageView &im, uint32_t
         rows |= RT::sweep_antiraster(hx, J, I, jb, lane);
     }
     if (rows) RT::store(im, y0, x0, J, rows, lane);
-    const bool active = RT::improvable(hx, J, I, jt, jb, lane);
+    const uint32_t self = RT::raise_max(hx, J, I, jt, jb, lane);
     RT::notify_scan(s, J, jt, jb, it, ib, lane);
     __threadfence();
     __syncwarp();
@@ -428,12 +472,12 @@ __device__ void scan_tile_reg(const EngineArgs &a, const ImageView &im, uint32_t
         const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
         if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x) {
             const uint32_t n = im.tile_base + (uint32_t)(ny * im.tiles_x + nx);
-            if (a.defer_push) mark_pending(a, n); else notify_tile(a, n);
+            if (a.defer_push) mark_pending(a, n); else notify_tile(a, n, level_of(a, im, s.misc[lane]));
         }
     }
     if (lane == 0) {
-        if (active) {
-            if (a.defer_push) mark_pending(a, t); else notify_tile(a, t);
+        if (self) {
+            if (a.defer_push) mark_pending(a, t); else notify_tile(a, t, level_of(a, im, self));
         }
         if (bad) set_status(a.hdr, kErrPrecondition);
         if (a.tile_work) atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
@@ -528,7 +572,7 @@ __device__ void visit_tile_reg(const EngineArgs &a, const ImageView &im, uint32_
 #if IWPP_TRACE
                 if (n < (uint32_t)kTraceTiles) atomicMax(&g_trace_gen[n], gen);
 #endif
-                notify_tile(a, n);
+                notify_tile(a, n, level_of(a, im, s.misc[lane]));
             }
         }
         const bool redo = finish_tile(a, t, lane);

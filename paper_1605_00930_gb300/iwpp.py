@@ -31,7 +31,7 @@ class IwppError(RuntimeError):
 class Plan(ctypes.Structure):
     _fields_ = [("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("sweeps", ctypes.c_int32),
                 ("revisit_sweeps", ctypes.c_int32), ("smem_queue_cap", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("local_solver", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("local_solver", ctypes.c_int32), ("value_levels", ctypes.c_int32),
                 ("watchdog_ns", ctypes.c_int64)]
 
     def as_dict(self):

@@ -77,11 +77,12 @@ def test_host_argument_errors_return_before_any_launch(iwpp):
     p = iwpp.iwpp_default_plan()
     p.smem_queue_cap = 8
     assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
-    # the register solver needs 64-column tiles of at most 16 rows; unknown solvers and a
-    # non-zero reserved field are rejected
-    for th, tw, solver, reserved in [(32, 32, 1, 0), (32, 64, 1, 0), (16, 64, 2, 0), (16, 64, 1, 1)]:
+    # the register solver needs 16 x 64 tiles; unknown solvers, value levels beyond 16 and
+    # value levels with the queue solver are rejected
+    for th, tw, solver, levels in [(32, 32, 1, 0), (32, 64, 1, 0), (16, 64, 2, 0), (16, 64, 1, 17),
+                                   (16, 64, 0, 4), (16, 64, 1, -1)]:
         p = iwpp.iwpp_default_plan()
-        p.tile_h, p.tile_w, p.local_solver, p.reserved = th, tw, solver, reserved
+        p.tile_h, p.tile_w, p.local_solver, p.value_levels = th, tw, solver, levels
         assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
     # missing / misaligned workspace
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, null, 16, null) == 3

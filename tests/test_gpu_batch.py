@@ -109,6 +109,17 @@ def test_mixed_batch_random_schedule(iw, oracle_lib):
     assert work[B.ntiles:].sum() > 0   # cycles recorded for the tiles
 
 
+def test_batch_rejects_value_levels(iw):
+    """Value-ordered tile queues are a single-image option: a batch call refuses the plan."""
+    cases = _mixed_cases(8, 2, max_side=300)
+    p = iw.iwpp_default_plan()
+    p.value_levels = 4
+    items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
+    B = iw.Batch(items)
+    import ctypes
+    assert iw.iwpp_reconstruct_batch(B.descs, p, ctypes.c_void_p(B.ws.data_ptr()), B.ws.numel(), None) == 1
+
+
 def test_batch_of_one_matches_single(iw, oracle_lib):
     c = synth.tissue_case(700, 900, nblobs=40)
     outs, _, _ = _run_batch(iw, [c])

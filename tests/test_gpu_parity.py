@@ -135,6 +135,22 @@ def test_plans_tissue_register(iw, oracle_lib, sweeps, bps):
         check(iw, oracle_lib, c.marker, c.mask, conn, "dilate", p)
 
 
+@pytest.mark.parametrize("levels", [2, 8, 16])
+@pytest.mark.parametrize("bps", [0, 6])
+def test_value_ordered_queue(iw, oracle_lib, levels, bps):
+    """Tile queues by value level (highest level first) reach the same fixed point."""
+    p = _plan(iw, value_levels=levels, blocks_per_sm=bps, **SOLVERS["register"])
+    c = synth.tissue_case(517, 700, nblobs=40)
+    for conn in (4, 8):
+        check(iw, oracle_lib, c.marker, c.mask, conn, "dilate", p)
+    field = synth.blob_field_u8(300, 451, 20, synth.rng_for(91, levels))
+    mask = synth.to_u16(field)
+    check(iw, oracle_lib, synth.fillholes_marker(mask), mask, 8, "erode", p)
+    check(iw, oracle_lib, synth.fillholes_marker(field), field, 4, "erode", p)
+    s = synth.sparse_seed_case(1024, 1536, nblobs=60, nseeds=12)
+    check(iw, oracle_lib, s.marker, s.mask, 8, "dilate", p)
+
+
 @pytest.mark.parametrize("revisit", [0, 2])
 @pytest.mark.parametrize("bps", [0, 1])
 def test_plans_fill_holes_u16(iw, oracle_lib, revisit, bps):

@@ -7,13 +7,17 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
 Contents
   * ``iwpp_oracle.c`` — Vincent's hybrid reconstruction (Sec. 3.1, Algorithm 7),
     single-threaded C, built here with gcc into ``liboracle.so``.
+  * ``edt_oracle.c`` — the Euclidean distance transform by Voronoi-site propagation
+    (Sec. 3.2, Algorithm 8) with a FIFO, in the same library.
   * ``bruteforce.py`` — Algorithm 1 (Jacobi iteration of Eq. "recon") in numpy.
   * ``features.py`` / ``mlp.py`` — plain numpy definitions of the per-tile
     features and of the 16-64-64-2 MLP used by the learned schedule.
 
 Parity status: reconstruction is pinned by brute force, hand-worked cases,
 invariants, duality, threshold decomposition and the binary special case
-(connected components); see tests/test_oracle_*.py.
+(connected components); the distance transform by the exact transform (brute force
+and scipy) as a lower bound, exactness for a single site, site validity and the
+local fixed point; see tests/test_oracle_*.py.
 """
 from __future__ import annotations
 
@@ -26,7 +30,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "iwpp_oracle.c")
+_SRCS = [os.path.join(_HERE, "iwpp_oracle.c"), os.path.join(_HERE, "edt_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -37,9 +41,9 @@ OPS = {"dilate": 0, "erode": 1}
 
 def build(force: bool = False) -> str:
     """Compile the C oracle with gcc (portable C11, no host-specific flags)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp] + _SRCS)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +62,9 @@ def _load():
                                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                                    ctypes.c_int]
             lib.oracle_precondition_ok.restype = ctypes.c_int
+            lib.oracle_edt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_edt.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -94,6 +101,24 @@ def precondition_ok(marker: np.ndarray, mask: np.ndarray, op: str = "dilate") ->
     if rc < 0:
         raise ValueError("bad argument")
     return rc == 1
+
+
+def edt(mask: np.ndarray, conn: int = 8, return_pops: bool = False):
+    """Distance transform by Voronoi-site propagation (Algorithm 8) of a 2-D mask
+    (non-zero = foreground). Returns (site, d2): int64 arrays, site = y * W + x of the
+    pixel's background site or -1, d2 = squared Euclidean distance to it or -1."""
+    if mask.ndim != 2:
+        raise ValueError("mask must be 2-D")
+    lib = _load()
+    fg = np.ascontiguousarray(mask != 0, dtype=np.uint8)
+    site = np.empty(fg.shape, np.int64)
+    d2 = np.empty(fg.shape, np.int64)
+    pops = ctypes.c_uint64(0)
+    rc = lib.oracle_edt(fg.ctypes.data, fg.shape[0], fg.shape[1], int(conn), site.ctypes.data, d2.ctypes.data,
+                        ctypes.byref(pops))
+    if rc != 0:
+        raise ValueError(f"oracle_edt failed with code {rc}")
+    return (site, d2, int(pops.value)) if return_pops else (site, d2)
 
 
 def reconstruct_many(items, threads: int | None = None):

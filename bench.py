@@ -251,6 +251,7 @@ def run_ours(args, rank: int, world: int):
     traffic = _traffic_from_profiles(dominant)
     cpu = cpu_baseline(cases, first_outputs) if rank == 0 and world == 1 and not args.no_cpu else None
     forms = run_forms(args, dev) if rank == 0 and world == 1 and not args.quick else None
+    edt = run_edt(args, dev, peak) if rank == 0 and world == 1 and not args.quick else None
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -273,6 +274,7 @@ def run_ours(args, rank: int, world: int):
         "clocks": cs.summary(t0, t1),
         "cpu_baseline": cpu,
         "forms": forms,
+        "edt": edt,
     }
     return out
 
@@ -327,6 +329,61 @@ def _timed(run, items, init, flush, reps, stream):
         if r > 0:
             ts.append(e0.elapsed_time(e1))
     return float(np.median(ts)), ts
+
+
+def run_edt(args, dev, peak):
+    """The distance transform (Algorithm 8 on the tile engine) on tissue-like masks: the
+    blob fields of the 4096^2 and 16384^2 workloads thresholded above 60 (objects = blobs).
+    Reports time, Gpixels/s, the HBM fraction of the compulsory 5 bytes per pixel (read the
+    mask, write the site map) and, against scipy's exact transform, the share of pixels
+    whose distance is exact and the largest error in pixels."""
+    import torch
+    from paper_1605_00930_gb300 import iwpp, synth
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, c in (("tissue4096", synth.tissue_case()), ("seeds16384_mask", None)):
+        mask = synth.sparse_seed_case().mask if c is None else c.mask
+        fg = (mask > 60).astype(np.uint8)
+        H, W = fg.shape
+        if H > 32767 or W > 32767:
+            continue
+        m = torch.from_numpy(fg).to(dev)
+        site = torch.empty((H, W), dtype=torch.int32, device=dev)
+        T = iwpp.DistanceTransform(H, W, dev)
+        ts = []
+        for r in range(max(3, args.form_reps) + 1):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if T(m, site, None, 8, stream) != 0:
+                raise RuntimeError("edt call failed")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                ts.append(e0.elapsed_time(e1))
+        if T.status(stream) != 0:
+            raise RuntimeError("edt device error")
+        ms = float(np.median(ts))
+        res = {"pixels": H * W, "foreground": round(float(fg.mean()), 4), "conn": 8, "ms": round(ms, 3),
+               "gpx_s": round(H * W / ms / 1e6, 3),
+               "hbm_frac": round(5 * H * W / (ms * 1e-3) / 1e9 / peak, 5)}
+        cnt = T.counters(stream)
+        res["visits"] = int(cnt["visits"])
+        if H * W <= 4096 * 4096:
+            try:
+                from scipy import ndimage
+                s = site.cpu().numpy().view(np.uint32).astype(np.int64)
+                yy, xx = np.mgrid[0:H, 0:W]
+                d2 = (yy - (s >> 16)) ** 2 + (xx - (s & 0xFFFF)) ** 2
+                ex = ndimage.distance_transform_edt(fg)
+                res["exact_fraction"] = round(float(np.mean(d2 == np.rint(ex ** 2))), 5)
+                res["max_error_px"] = round(float(np.max(np.sqrt(d2) - ex)), 4)
+            except ImportError:
+                pass
+        out[name] = res
+        del m, site, T
+    return out
 
 
 def run_forms(args, dev):

@@ -108,6 +108,9 @@ _PROTOS = [
     ("iwpp_reconstruct_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.POINTER(ctypes.c_int)]),
+    ("iwpp_edt_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
+    ("iwpp_edt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("iwpp_sync_status", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("iwpp_work_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -281,6 +284,42 @@ def iwpp_reconstruct_noalloc(marker_ptr, mask_ptr, H, W, conn, op, dtype, stream
 
 def iwpp_sync_status(ws_ptr, stream) -> int:
     return lib().iwpp_sync_status(ws_ptr, stream)
+
+
+def iwpp_edt_workspace_bytes(H: int, W: int) -> int:
+    return int(lib().iwpp_edt_workspace_bytes(H, W))
+
+
+def iwpp_edt(mask_ptr, site_ptr, dist2_ptr, H, W, conn, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_edt(mask_ptr, site_ptr, dist2_ptr, H, W, conn, ws_ptr, ws_bytes, stream)
+
+
+class DistanceTransform:
+    """Reusable distance transform (Algorithm 8) for H x W masks: holds the workspace.
+    Call with a CUDA uint8 mask (non-zero = foreground) and int32 tensors for the sites
+    (packed (y << 16) | x, -1 = none) and, optionally, the squared distances."""
+
+    def __init__(self, H: int, W: int, device=None):
+        import torch
+        self.H, self.W = int(H), int(W)
+        n = iwpp_edt_workspace_bytes(self.H, self.W)
+        if n == 0:
+            raise ValueError("image size not supported (1 .. 32767 per side)")
+        self.ws = alloc_workspace(n, device or torch.device("cuda"))
+
+    def __call__(self, mask, site, dist2=None, conn: int = 8, stream=None) -> int:
+        for t in (mask, site) + ((dist2,) if dist2 is not None else ()):
+            if tuple(t.shape) != (self.H, self.W) or not t.is_contiguous():
+                raise ValueError("shape mismatch or non-contiguous tensor")
+        return iwpp_edt(ctypes.c_void_p(mask.data_ptr()), ctypes.c_void_p(site.data_ptr()),
+                        ctypes.c_void_p(dist2.data_ptr()) if dist2 is not None else None, self.H, self.W,
+                        int(conn), ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), _stream_handle(stream))
+
+    def status(self, stream=None) -> int:
+        return iwpp_sync_status(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
+
+    def counters(self, stream=None):
+        return iwpp_work_counters(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
 
 
 def iwpp_work_counters(ws_ptr, stream):

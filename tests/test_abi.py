@@ -89,6 +89,22 @@ def test_host_argument_errors_return_before_any_launch(iwpp):
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, P(ws + 16), 16, null) == 3
 
 
+def test_edt_host_errors_return_before_any_launch(iwpp):
+    buf = (ctypes.c_uint8 * 4096)()
+    a = ctypes.addressof(buf)
+    a16 = (a + 15) // 16 * 16
+    ws = (a + 255) // 256 * 256 if a % 256 else a
+    P, null = ctypes.c_void_p, ctypes.c_void_p(0)
+    assert iwpp.iwpp_edt_workspace_bytes(40000, 10) == 0 and iwpp.iwpp_edt_workspace_bytes(0, 5) == 0
+    assert iwpp.iwpp_edt_workspace_bytes(100, 100) > 0
+    assert iwpp.iwpp_edt(null, P(a16), null, 4, 4, 8, P(ws), 4096, null) == 1          # no mask
+    assert iwpp.iwpp_edt(P(a16), P(a16), null, 4, 4, 6, P(ws), 4096, null) == 1        # connectivity
+    assert iwpp.iwpp_edt(P(a16), P(a16 + 2), null, 4, 4, 8, P(ws), 4096, null) == 1    # misaligned sites
+    assert iwpp.iwpp_edt(P(a16), P(a16), null, 40000, 4, 8, P(ws), 4096, null) == 1    # too large
+    assert iwpp.iwpp_edt(P(a16), P(a16), null, 4, 4, 8, null, 4096, null) == 3         # no workspace
+    assert iwpp.iwpp_edt(P(a16), P(a16), null, 4, 4, 8, P(ws), 16, null) == 3          # workspace too small
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     import importlib
     from paper_1605_00930_gb300 import iwpp as m

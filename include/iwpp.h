@@ -18,7 +18,8 @@
  *     in DEVICE memory, base address 16-byte aligned. The caller owns them.
  *   - marker_inout holds J on entry and R on exit (the paper's J is both
  *     input and output). mask is only read.
- *   - H >= 1, W >= 1, H * W < 2^32 per image; connectivity is 4 or 8 (the
+ *   - 1 <= H, W < 2^31 and H * W < 2^40 per image (a 100000 x 100000 image is
+ *     fine; the device must hold it); connectivity is 4 or 8 (the
  *     hexagonal 6-connectivity that Sec. 2.1.2 also names is not supported).
  *   - The workspace is caller-owned device memory of at least the size the
  *     matching *_workspace_bytes call returns, 256-byte aligned. The library

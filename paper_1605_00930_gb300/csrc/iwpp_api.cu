@@ -189,9 +189,11 @@ void default_plan(iwpp_plan *p) {
     p->watchdog_ns = 0;
 }
 
+// Pixel offsets are 64-bit everywhere; sides stay below 2^31 (ints in the kernels) and
+// the pixel count below 2^40, which keeps the tile count of any plan below 2^31.
 static bool image_ok(int64_t H, int64_t W) {
     return H >= 1 && W >= 1 && H < (1ll << 31) && W < (1ll << 31) &&
-           (uint64_t)H * (uint64_t)W < (1ull << 32);
+           (uint64_t)H * (uint64_t)W < (1ull << 40);
 }
 
 static ImageView make_view(void *marker, const void *mask, int64_t H, int64_t W, int conn, int op, int dtype,

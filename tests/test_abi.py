@@ -66,7 +66,8 @@ def test_host_argument_errors_return_before_any_launch(iwpp):
     assert iwpp.iwpp_reconstruct(P(a16 + 1), P(a16), 4, 4, 8, 0, 0, P(ws), 16, null) == 1
     # bad sizes, connectivity, op, dtype
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 0, 4, 8, 0, 0, P(ws), 16, null) == 1
-    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 1 << 16, 1 << 16, 8, 0, 0, P(ws), 16, null) == 1
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 1 << 21, 1 << 20, 8, 0, 0, P(ws), 16, null) == 1   # 2^41 px
+    assert iwpp.iwpp_reconstruct(P(a16), P(a16), 1 << 31, 1, 8, 0, 0, P(ws), 16, null) == 1
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 6, 0, 0, P(ws), 16, null) == 1
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 2, 0, P(ws), 16, null) == 1
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 3, P(ws), 16, null) == 1

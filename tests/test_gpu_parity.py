@@ -178,6 +178,31 @@ def test_sparse_seeds_16384(iw, oracle_lib):
     check(iw, oracle_lib, c.marker, c.mask, 8, "dilate")
 
 
+@pytest.mark.parametrize("conn", [8])
+def test_image_beyond_2_32_pixels(iw, oracle_lib, conn):
+    """A 65664 x 65664 u8 image (4.3 G pixels, more than 2^32): 128 x 128 copies of a
+    tissue crop, each followed by a zero-mask gutter row and column, so no value can cross
+    from one copy to another and the result must be the oracle's result for one copy,
+    repeated. Exercises 64-bit pixel offsets everywhere on the path."""
+    c = synth.tissue_case(512, 512, nblobs=8)
+    mk = np.zeros((513, 513), np.uint8)
+    ms = np.zeros((513, 513), np.uint8)
+    mk[:512, :512] = c.marker
+    ms[:512, :512] = c.mask
+    exp = oracle_lib.reconstruct(mk, ms, conn, "dilate")
+    reps = 128
+    M = torch.from_numpy(mk).cuda().repeat(reps, reps)
+    I = torch.from_numpy(ms).cuda().repeat(reps, reps)
+    H, W = M.shape
+    assert H * W > 2 ** 32
+    R = iw.Reconstructor(H, W, torch.uint8)
+    assert R(M, I, conn, "dilate") == 0
+    assert R.status() == 0
+    del I, R
+    E = torch.from_numpy(exp).cuda()
+    assert torch.equal(M.view(reps, 513, reps, 513), E[None, :, None, :].expand(reps, 513, reps, 513))
+
+
 def test_repeatable_output(iw, oracle_lib):
     c = synth.tissue_case(777, 1031, nblobs=60)
     exp = oracle_lib.reconstruct(c.marker, c.mask, 8, "dilate")

@@ -109,16 +109,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside)}
 
 
+# The sources the reconstruction kernels are built and launched from (their digest keys the
+# ncu traffic record: a change to any of them makes the record stale).
+KERNEL_SOURCES = ["paper_1605_00930_gb300/csrc/iwpp_api.cu",
+                  "paper_1605_00930_gb300/csrc/iwpp_engine.cuh", "paper_1605_00930_gb300/csrc/iwpp_host.h",
+                  "paper_1605_00930_gb300/csrc/iwpp_kern_reg.cu", "paper_1605_00930_gb300/csrc/iwpp_regtile.cuh"]
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_from_profiles(kernel: str):
-    """ncu DRAM bytes per launch recorded under profiles/ for the current source."""
+    """ncu DRAM bytes per launch recorded under profiles/ for the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    import hashlib
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1605_00930_gb300", "csrc"))):
-        h.update(open(os.path.join(ROOT, "paper_1605_00930_gb300", "csrc", f), "rb").read())
-    digest = h.hexdigest()[:16]
+    digest = kernel_digest()
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:

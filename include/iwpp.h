@@ -359,6 +359,29 @@ IWPP_API int iwpp_reconstruct_noalloc(void *marker_inout, const void *mask, int6
                                       int connectivity, int op, int dtype, void *stream, int *status_out);
 
 /*
+ * Operators built on reconstruction by dilation (the paper names further IWPP
+ * operators as future work; these are the reconstruction-based ones). Each builds
+ * its marker on the device, runs one reconstruction exactly as iwpp_reconstruct
+ * (default plan; same workspace size, iwpp_workspace_bytes(H, W, dtype, NULL)) and
+ * finishes with an elementwise kernel, all on `stream`. image, out and scratch are
+ * device buffers of H x W pixels of `dtype` (out of iwpp_regional_maxima: uint8),
+ * 16-byte aligned; image is only read.
+ *   iwpp_hmaxima          out = R_image(max(image - h, 0)): the h-maxima transform
+ *                         (every regional maximum lowered by h, clipped at its saddle)
+ *   iwpp_hdome            out = image - R_image(max(image - h, 0)): the domes of
+ *                         height up to h that the h-maxima transform removes
+ *   iwpp_regional_maxima  out[p] = 1 where image(p) > R_image(image - 1)(p), else 0:
+ *                         the plateaus whose every outside neighbour is strictly lower;
+ *                         scratch receives R_image(image - 1)
+ */
+IWPP_API int iwpp_hmaxima(const void *image, void *out, int64_t H, int64_t W, uint32_t h, int connectivity,
+                          int dtype, void *workspace, size_t ws_bytes, void *stream);
+IWPP_API int iwpp_hdome(const void *image, void *out, int64_t H, int64_t W, uint32_t h, int connectivity,
+                        int dtype, void *workspace, size_t ws_bytes, void *stream);
+IWPP_API int iwpp_regional_maxima(const void *image, void *scratch, uint8_t *out, int64_t H, int64_t W,
+                                  int connectivity, int dtype, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Euclidean distance transform by wavefront propagation of Voronoi sites (Sec. 3.2,
  * Algorithm 8) on the same persistent tile engine. Background pixels (mask == 0) are
  * their own sites; every other pixel ends with the site, among those its neighbours

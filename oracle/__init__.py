@@ -12,6 +12,8 @@ Contents
   * ``bruteforce.py`` — Algorithm 1 (Jacobi iteration of Eq. "recon") in numpy.
   * ``features.py`` / ``mlp.py`` — plain numpy definitions of the per-tile
     features and of the 16-64-64-2 MLP used by the learned schedule.
+  * ``ops.py`` — h-maxima, h-dome and regional maxima as compositions of the
+    reconstruction, and regional maxima once more by plateau flooding.
 
 Parity status: reconstruction is pinned by brute force, hand-worked cases,
 invariants, duality, threshold decomposition and the binary special case

@@ -108,6 +108,15 @@ _PROTOS = [
     ("iwpp_reconstruct_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.POINTER(ctypes.c_int)]),
+    ("iwpp_hmaxima", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_void_p]),
+    ("iwpp_hdome", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                  ctypes.c_void_p]),
+    ("iwpp_regional_maxima", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_size_t, ctypes.c_void_p]),
     ("iwpp_edt_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     ("iwpp_edt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -284,6 +293,60 @@ def iwpp_reconstruct_noalloc(marker_ptr, mask_ptr, H, W, conn, op, dtype, stream
 
 def iwpp_sync_status(ws_ptr, stream) -> int:
     return lib().iwpp_sync_status(ws_ptr, stream)
+
+
+def iwpp_hmaxima(image_ptr, out_ptr, H, W, h, conn, dtype, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_hmaxima(image_ptr, out_ptr, H, W, h, conn, dtype, ws_ptr, ws_bytes, stream)
+
+
+def iwpp_hdome(image_ptr, out_ptr, H, W, h, conn, dtype, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_hdome(image_ptr, out_ptr, H, W, h, conn, dtype, ws_ptr, ws_bytes, stream)
+
+
+def iwpp_regional_maxima(image_ptr, scratch_ptr, out_ptr, H, W, conn, dtype, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_regional_maxima(image_ptr, scratch_ptr, out_ptr, H, W, conn, dtype, ws_ptr, ws_bytes, stream)
+
+
+def _op_ws(image):
+    return alloc_workspace(iwpp_workspace_bytes(image.shape[0], image.shape[1], _dtype_code(image)), image.device)
+
+
+def hmaxima(image, h: int, conn: int = 8, stream=None):
+    """h-maxima transform of a CUDA uint8/uint16 image (a new tensor)."""
+    import torch
+    out = torch.empty_like(image)
+    ws = _op_ws(image)
+    _check(iwpp_hmaxima(ctypes.c_void_p(image.data_ptr()), ctypes.c_void_p(out.data_ptr()), image.shape[0],
+                        image.shape[1], int(h), int(conn), _dtype_code(image), ctypes.c_void_p(ws.data_ptr()),
+                        ws.numel(), _stream_handle(stream)), "iwpp_hmaxima")
+    _check(iwpp_sync_status(ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "device")
+    return out
+
+
+def hdome(image, h: int, conn: int = 8, stream=None):
+    """h-dome transform: image - hmaxima(image, h) (a new tensor)."""
+    import torch
+    out = torch.empty_like(image)
+    ws = _op_ws(image)
+    _check(iwpp_hdome(ctypes.c_void_p(image.data_ptr()), ctypes.c_void_p(out.data_ptr()), image.shape[0],
+                      image.shape[1], int(h), int(conn), _dtype_code(image), ctypes.c_void_p(ws.data_ptr()),
+                      ws.numel(), _stream_handle(stream)), "iwpp_hdome")
+    _check(iwpp_sync_status(ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "device")
+    return out
+
+
+def regional_maxima(image, conn: int = 8, stream=None):
+    """uint8 mask of the regional maxima of a CUDA uint8/uint16 image."""
+    import torch
+    scratch = torch.empty_like(image)
+    out = torch.empty(image.shape, dtype=torch.uint8, device=image.device)
+    ws = _op_ws(image)
+    _check(iwpp_regional_maxima(ctypes.c_void_p(image.data_ptr()), ctypes.c_void_p(scratch.data_ptr()),
+                                ctypes.c_void_p(out.data_ptr()), image.shape[0], image.shape[1], int(conn),
+                                _dtype_code(image), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                _stream_handle(stream)), "iwpp_regional_maxima")
+    _check(iwpp_sync_status(ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "device")
+    return out
 
 
 def iwpp_edt_workspace_bytes(H: int, W: int) -> int:

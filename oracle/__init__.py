@@ -9,6 +9,8 @@ Contents
     single-threaded C, built here with gcc into ``liboracle.so``.
   * ``edt_oracle.c`` — the Euclidean distance transform by Voronoi-site propagation
     (Sec. 3.2, Algorithm 8) with a FIFO, in the same library.
+  * ``wshed_oracle.c`` — marker-controlled watershed by flooding as an IWPP propagation of
+    (level, label) pairs, in the same library.
   * ``bruteforce.py`` — Algorithm 1 (Jacobi iteration of Eq. "recon") in numpy.
   * ``features.py`` / ``mlp.py`` — plain numpy definitions of the per-tile
     features and of the 16-64-64-2 MLP used by the learned schedule.
@@ -32,7 +34,8 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "iwpp_oracle.c"), os.path.join(_HERE, "edt_oracle.c")]
+_SRCS = [os.path.join(_HERE, "iwpp_oracle.c"), os.path.join(_HERE, "edt_oracle.c"),
+         os.path.join(_HERE, "wshed_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -67,6 +70,10 @@ def _load():
             lib.oracle_edt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
             lib.oracle_edt.restype = ctypes.c_int
+            lib.oracle_watershed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_watershed.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -121,6 +128,25 @@ def edt(mask: np.ndarray, conn: int = 8, return_pops: bool = False):
     if rc != 0:
         raise ValueError(f"oracle_edt failed with code {rc}")
     return (site, d2, int(pops.value)) if return_pops else (site, d2)
+
+
+def watershed(markers: np.ndarray, gradient: np.ndarray, conn: int = 8, return_pops: bool = False):
+    """Flooding of `gradient` from labelled `markers` (uint32, 0 = none, 1..65534): returns
+    (label uint32, level int32) — a label reaching each pixel at its minimax flooding level
+    (which of several is order-dependent), and that level (0 / -1 where no marker reaches)."""
+    if markers.shape != gradient.shape or markers.ndim != 2 or gradient.dtype not in DTYPES:
+        raise ValueError("markers and a uint8/uint16 gradient of the same 2-D shape")
+    lib = _load()
+    mk = np.ascontiguousarray(markers, dtype=np.uint32)
+    g = np.ascontiguousarray(gradient)
+    label = np.empty(mk.shape, np.uint32)
+    level = np.empty(mk.shape, np.int32)
+    pops = ctypes.c_uint64(0)
+    rc = lib.oracle_watershed(mk.ctypes.data, g.ctypes.data, DTYPES[g.dtype], mk.shape[0], mk.shape[1], int(conn),
+                              label.ctypes.data, level.ctypes.data, ctypes.byref(pops))
+    if rc != 0:
+        raise ValueError(f"oracle_watershed failed with code {rc}")
+    return (label, level, int(pops.value)) if return_pops else (label, level)
 
 
 def reconstruct_many(items, threads: int | None = None):

@@ -263,6 +263,7 @@ def run_ours(args, rank: int, world: int):
     cpu = cpu_baseline(cases, first_outputs) if rank == 0 and world == 1 and not args.no_cpu else None
     forms = run_forms(args, dev) if rank == 0 and world == 1 and not args.quick else None
     edt = run_edt(args, dev, peak) if rank == 0 and world == 1 and not args.quick else None
+    wshed = run_watershed(args, dev) if rank == 0 and world == 1 and not args.quick else None
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -286,6 +287,7 @@ def run_ours(args, rank: int, world: int):
         "cpu_baseline": cpu,
         "forms": forms,
         "edt": edt,
+        "watershed": wshed,
     }
     return out
 
@@ -395,6 +397,49 @@ def run_edt(args, dev, peak):
         out[name] = res
         del m, site, T
     return out
+
+
+def run_watershed(args, dev):
+    """Marker-controlled watershed by flooding on the 4096^2 tissue image: the gradient is
+    the inverted blob field (blobs become basins), 2000 seeded markers with distinct labels.
+    Reports time and Gpixels/s of the whole call (initialisation, flooding, labels)."""
+    import torch
+    from paper_1605_00930_gb300 import iwpp, synth
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    f = synth.tissue_case().mask
+    grad = torch.from_numpy((255 - f).astype(np.uint8)).to(dev)
+    H, W = f.shape
+    rng = synth.rng_for(9)
+    markers = np.zeros((H, W), np.int32)
+    markers[rng.integers(0, H, 2000), rng.integers(0, W, 2000)] = np.arange(1, 2001)
+    mk = torch.from_numpy(markers).to(dev)
+    labels = torch.empty((H, W), dtype=torch.int32, device=dev)
+    ws = iwpp.alloc_workspace(iwpp.iwpp_watershed_workspace_bytes(H, W), dev)
+    ts = []
+    for r in range(max(3, args.form_reps) + 1):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = iwpp.iwpp_watershed(ctypes_ptr(mk), ctypes_ptr(grad), iwpp.IWPP_U8, ctypes_ptr(labels), None, H, W, 8,
+                                 ctypes_ptr(ws), ws.numel(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise RuntimeError("watershed call failed")
+        if r > 0:
+            ts.append(e0.elapsed_time(e1))
+    if iwpp.iwpp_sync_status(ctypes_ptr(ws), stream.cuda_stream) != 0:
+        raise RuntimeError("watershed device error")
+    ms = float(np.median(ts))
+    cnt = iwpp.iwpp_work_counters(ctypes_ptr(ws), stream.cuda_stream)
+    return {"tissue4096": {"pixels": H * W, "markers": 2000, "conn": 8, "ms": round(ms, 3),
+                           "gpx_s": round(H * W / ms / 1e6, 3), "visits": int(cnt["visits"])}}
+
+
+def ctypes_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def run_forms(args, dev):

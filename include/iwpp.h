@@ -382,6 +382,31 @@ IWPP_API int iwpp_regional_maxima(const void *image, void *scratch, uint8_t *out
                                   int connectivity, int dtype, void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Marker-controlled watershed by flooding, as an IWPP propagation on the same tile engine
+ * (watershed is one of the operators the paper names as future work for the pattern).
+ * Every pixel carries a pair (level, label): a marker pixel is fixed at (its gradient,
+ * its label), every other pixel starts unreached; a neighbour q offers p the pair
+ * (max(level(q), gradient(p)), label(q)) and p keeps the lexicographically smallest.
+ * The levels reached are unique: the minimax flooding level (the reconstruction by
+ * erosion of the marker levels under the gradient). Which label a pixel gets when several
+ * markers reach it at its level depends on the order of work, as in any flooding
+ * watershed; every result has each label's markers reaching its pixels at their level.
+ * No watershed lines are drawn.
+ *   markers      device, H x W uint32: 0 = none, 1 .. 65534 = label (larger labels make
+ *                the device status IWPP_ERR_ARG)
+ *   gradient     device, H x W of `dtype` (u8 or u16)
+ *   labels_out   device, H x W uint32, 4-byte aligned: the label of each pixel (0 where
+ *                no marker reaches, i.e. no marker at all); also the working buffer
+ *   levels_out   device, H x W int32 or NULL: the flooding level (-1 where unreached)
+ *   H, W         1 <= H, W < 2^31, H * W < 2^40
+ *   workspace    device, 256-byte aligned, iwpp_watershed_workspace_bytes(H, W) bytes
+ */
+IWPP_API size_t iwpp_watershed_workspace_bytes(int64_t H, int64_t W);
+IWPP_API int iwpp_watershed(const uint32_t *markers, const void *gradient, int dtype, uint32_t *labels_out,
+                            int32_t *levels_out, int64_t H, int64_t W, int connectivity, void *workspace,
+                            size_t ws_bytes, void *stream);
+
+/*
  * Euclidean distance transform by wavefront propagation of Voronoi sites (Sec. 3.2,
  * Algorithm 8) on the same persistent tile engine. Background pixels (mask == 0) are
  * their own sites; every other pixel ends with the site, among those its neighbours

@@ -117,6 +117,10 @@ _PROTOS = [
     ("iwpp_regional_maxima", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_watershed_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
+    ("iwpp_watershed", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("iwpp_edt_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     ("iwpp_edt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -347,6 +351,36 @@ def regional_maxima(image, conn: int = 8, stream=None):
                                 _stream_handle(stream)), "iwpp_regional_maxima")
     _check(iwpp_sync_status(ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "device")
     return out
+
+
+def iwpp_watershed_workspace_bytes(H: int, W: int) -> int:
+    return int(lib().iwpp_watershed_workspace_bytes(H, W))
+
+
+def iwpp_watershed(markers_ptr, grad_ptr, dtype, labels_ptr, levels_ptr, H, W, conn, ws_ptr, ws_bytes,
+                   stream) -> int:
+    return lib().iwpp_watershed(markers_ptr, grad_ptr, dtype, labels_ptr, levels_ptr, H, W, conn, ws_ptr, ws_bytes,
+                                stream)
+
+
+def watershed(markers, gradient, conn: int = 8, with_levels: bool = False, stream=None):
+    """Marker-controlled watershed by flooding: markers (CUDA int32/uint32 labels, 0 =
+    none) over a CUDA uint8/uint16 gradient. Returns the labels (int32), and the flooding
+    levels too when asked."""
+    import torch
+    if markers.shape != gradient.shape:
+        raise ValueError("shape mismatch")
+    H, W = gradient.shape
+    labels = torch.empty((H, W), dtype=torch.int32, device=gradient.device)
+    levels = torch.empty((H, W), dtype=torch.int32, device=gradient.device) if with_levels else None
+    ws = alloc_workspace(iwpp_watershed_workspace_bytes(H, W), gradient.device)
+    mk = markers.contiguous()
+    _check(iwpp_watershed(ctypes.c_void_p(mk.data_ptr()), ctypes.c_void_p(gradient.data_ptr()),
+                          _dtype_code(gradient), ctypes.c_void_p(labels.data_ptr()),
+                          ctypes.c_void_p(levels.data_ptr()) if levels is not None else None, H, W, int(conn),
+                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream)), "iwpp_watershed")
+    _check(iwpp_sync_status(ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "device")
+    return (labels, levels) if with_levels else labels
 
 
 def iwpp_edt_workspace_bytes(H: int, W: int) -> int:

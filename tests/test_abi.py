@@ -106,6 +106,27 @@ def test_edt_host_errors_return_before_any_launch(iwpp):
     assert iwpp.iwpp_edt(P(a16), P(a16), null, 4, 4, 8, P(ws), 16, null) == 3          # workspace too small
 
 
+def test_watershed_and_operator_host_errors(iwpp):
+    buf = (ctypes.c_uint8 * 4096)()
+    a = ctypes.addressof(buf)
+    a16 = (a + 15) // 16 * 16
+    ws = (a + 255) // 256 * 256 if a % 256 else a
+    P, null = ctypes.c_void_p, ctypes.c_void_p(0)
+    assert iwpp.iwpp_watershed_workspace_bytes(0, 4) == 0 and iwpp.iwpp_watershed_workspace_bytes(1 << 31, 1) == 0
+    assert iwpp.iwpp_watershed_workspace_bytes(64, 64) > 0
+    assert iwpp.iwpp_watershed(null, P(a16), 0, P(a16), null, 4, 4, 8, P(ws), 4096, null) == 1      # no markers
+    assert iwpp.iwpp_watershed(P(a16), P(a16), 2, P(a16), null, 4, 4, 8, P(ws), 4096, null) == 1    # dtype
+    assert iwpp.iwpp_watershed(P(a16), P(a16), 0, P(a16), null, 4, 4, 5, P(ws), 4096, null) == 1    # connectivity
+    assert iwpp.iwpp_watershed(P(a16), P(a16), 0, P(a16 + 1), null, 4, 4, 8, P(ws), 4096, null) == 1
+    assert iwpp.iwpp_watershed(P(a16), P(a16), 0, P(a16), null, 4, 4, 8, null, 4096, null) == 3
+    assert iwpp.iwpp_watershed(P(a16), P(a16), 0, P(a16), null, 4, 4, 8, P(ws), 8, null) == 3
+    for fn in (iwpp.iwpp_hmaxima, iwpp.iwpp_hdome):
+        assert fn(null, P(a16), 4, 4, 3, 8, 0, P(ws), 4096, null) == 1
+        assert fn(P(a16 + 1), P(a16), 4, 4, 3, 8, 0, P(ws), 4096, null) == 1
+        assert fn(P(a16), P(a16), 4, 4, 3, 8, 7, P(ws), 4096, null) == 1
+    assert iwpp.iwpp_regional_maxima(P(a16), P(a16), null, 4, 4, 8, 0, P(ws), 4096, null) == 1
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     import importlib
     from paper_1605_00930_gb300 import iwpp as m

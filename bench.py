@@ -137,6 +137,22 @@ def _traffic_from_profiles(kernel: str):
     return None
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time: every rank of the replicas contributes, all get the max."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gpx_s(world: int, pix_per_step: int, ms_per_step: float) -> float:
+    """Whole-job throughput of `world` replicas, each doing `pix_per_step` pixels per step,
+    timed by the slowest rank."""
+    return world * pix_per_step / (ms_per_step * 1e-3) / 1e9
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_1605_00930_gb300 import build as B
@@ -213,11 +229,8 @@ def run_ours(args, rank: int, world: int):
     drain_ms = sum(e[k][1].elapsed_time(e[k][2]) for e in evs for k in range(len(dev_cases)))
     total_ms = scan_ms + drain_ms
     ms_per_step = total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms_per_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = world * pix_per_step / (ms_per_step * 1e-3) / 1e9
+    ms_per_step = max_over_ranks(ms_per_step, world, dev)
+    value = job_gpx_s(world, pix_per_step, ms_per_step)
 
     # end to end through the public call with host buffers
     host_in = [(torch.from_numpy(c[0]).pin_memory(), torch.from_numpy(c[1]).pin_memory()) for c in cases]

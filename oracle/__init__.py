@@ -11,6 +11,8 @@ Contents
     (Sec. 3.2, Algorithm 8) with a FIFO, in the same library.
   * ``wshed_oracle.c`` — marker-controlled watershed by flooding as an IWPP propagation of
     (level, label) pairs, in the same library.
+  * ``skiz_oracle.c`` — the geodesic skeleton by influence zones (multi-source
+    breadth-first propagation of (distance, label set)), in the same library.
   * ``bruteforce.py`` — Algorithm 1 (Jacobi iteration of Eq. "recon") in numpy.
   * ``features.py`` / ``mlp.py`` — plain numpy definitions of the per-tile
     features and of the 16-64-64-2 MLP used by the learned schedule.
@@ -21,7 +23,9 @@ Parity status: reconstruction is pinned by brute force, hand-worked cases,
 invariants, duality, threshold decomposition and the binary special case
 (connected components); the distance transform by the exact transform (brute force
 and scipy) as a lower bound, exactness for a single site, site validity and the
-local fixed point; see tests/test_oracle_*.py.
+local fixed point; the watershed's levels by brute-force relaxation and the erosion
+reconstruction; the SKIZ by per-marker brute-force distances and scipy's chamfer
+distance transform; see tests/test_oracle_*.py.
 """
 from __future__ import annotations
 
@@ -35,7 +39,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, "iwpp_oracle.c"), os.path.join(_HERE, "edt_oracle.c"),
-         os.path.join(_HERE, "wshed_oracle.c")]
+         os.path.join(_HERE, "wshed_oracle.c"), os.path.join(_HERE, "skiz_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -74,6 +78,10 @@ def _load():
                                              ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.POINTER(ctypes.c_uint64)]
             lib.oracle_watershed.restype = ctypes.c_int
+            lib.oracle_skiz.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_skiz.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -147,6 +155,29 @@ def watershed(markers: np.ndarray, gradient: np.ndarray, conn: int = 8, return_p
     if rc != 0:
         raise ValueError(f"oracle_watershed failed with code {rc}")
     return (label, level, int(pops.value)) if return_pops else (label, level)
+
+
+def skiz(markers: np.ndarray, mask: np.ndarray, conn: int = 8, return_pops: bool = False):
+    """Geodesic influence zones of labelled `markers` (uint32, 0 = none, 1..65534) inside the
+    domain mask != 0 or marker != 0: returns a dict of int32 ``dist`` (-1 = unreached) and
+    uint32 ``lmin``, ``lmax`` (smallest / largest label among the nearest markers, 0 = unreached)
+    and ``zone`` (the label where lmin == lmax, 0 on the skeleton and where unreached)."""
+    if markers.shape != mask.shape or markers.ndim != 2:
+        raise ValueError("markers and mask of the same 2-D shape")
+    lib = _load()
+    mk = np.ascontiguousarray(markers, dtype=np.uint32)
+    m = np.ascontiguousarray(mask != 0, dtype=np.uint8)
+    out = {"dist": np.empty(mk.shape, np.int32), "lmin": np.empty(mk.shape, np.uint32),
+           "lmax": np.empty(mk.shape, np.uint32), "zone": np.empty(mk.shape, np.uint32)}
+    pops = ctypes.c_uint64(0)
+    rc = lib.oracle_skiz(mk.ctypes.data, m.ctypes.data, mk.shape[0], mk.shape[1], int(conn),
+                         out["dist"].ctypes.data, out["lmin"].ctypes.data, out["lmax"].ctypes.data,
+                         out["zone"].ctypes.data, ctypes.byref(pops))
+    if rc != 0:
+        raise ValueError(f"oracle_skiz failed with code {rc}")
+    if return_pops:
+        out["pops"] = int(pops.value)
+    return out
 
 
 def reconstruct_many(items, threads: int | None = None):

@@ -211,14 +211,16 @@ def test_repeatable_output(iw, oracle_lib):
         np.testing.assert_array_equal(got, exp)
 
 
-def test_precondition_violation_reported(iw):
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
+def test_precondition_violation_reported(iw, solver):
+    p = _plan(iw, **SOLVERS[solver])
     mask = np.full((70, 90), 10, np.uint8)
     marker = np.zeros_like(mask)
     marker[33, 44] = 11
-    gpu_run(iw, marker, mask, 8, "dilate", expect_status=2)
+    gpu_run(iw, marker, mask, 8, "dilate", p, expect_status=2)
     up = np.full_like(mask, 10)
     up[5, 6] = 9
-    gpu_run(iw, up, mask, 8, "erode", expect_status=2)
+    gpu_run(iw, up, mask, 8, "erode", p, expect_status=2)
 
 
 def test_workspace_too_small(iw):
@@ -234,15 +236,16 @@ def test_workspace_too_small(iw):
     assert iw.iwpp_sync_status(P(ws.data_ptr()), s) == 0
 
 
-def test_watchdog_timeout_returns_and_workspace_recovers(iw, oracle_lib):
+@pytest.mark.parametrize("solver", ["register", "queue"])
+def test_watchdog_timeout_returns_and_workspace_recovers(iw, oracle_lib, solver):
     """A 1 ns watchdog makes an idle CTA's wait for work run out: the kernel records
     IWPP_ERR_TIMEOUT and returns (no hang, no trap); the same workspace then serves a
-    normal call."""
+    normal call. Both local solvers share the queue protocol; both are exercised."""
     c = synth.tissue_case(256, 1024, nblobs=40)
-    p = _plan(iw, watchdog_ns=1, sweeps=0, blocks_per_sm=1)
+    p = _plan(iw, watchdog_ns=1, sweeps=0, blocks_per_sm=1, **SOLVERS[solver])
     dt = torch.uint8
     seen = set()
-    R = iw.Reconstructor(256, 1024, dt)   # workspace sized for the default plan (the larger)
+    R = iw.Reconstructor(256, 1024, dt, p)
     R.plan = p
     for _ in range(5):
         m = torch.from_numpy(c.marker).cuda()
@@ -253,7 +256,7 @@ def test_watchdog_timeout_returns_and_workspace_recovers(iw, oracle_lib):
             break
     assert 5 in seen, seen
     torch.cuda.synchronize()
-    R.plan = None
+    R.plan = _plan(iw, **SOLVERS[solver])
     m = torch.from_numpy(c.marker).cuda()
     I = torch.from_numpy(c.mask).cuda()
     assert R(m, I, 8, "dilate") == 0

@@ -277,6 +277,7 @@ def run_ours(args, rank: int, world: int):
     forms = run_forms(args, dev) if rank == 0 and world == 1 and not args.quick else None
     edt = run_edt(args, dev, peak) if rank == 0 and world == 1 and not args.quick else None
     wshed = run_watershed(args, dev) if rank == 0 and world == 1 and not args.quick else None
+    skiz = run_skiz(args, dev) if rank == 0 and world == 1 and not args.quick else None
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -301,6 +302,7 @@ def run_ours(args, rank: int, world: int):
         "forms": forms,
         "edt": edt,
         "watershed": wshed,
+        "skiz": skiz,
     }
     return out
 
@@ -447,6 +449,41 @@ def run_watershed(args, dev):
     ms = float(np.median(ts))
     cnt = iwpp.iwpp_work_counters(ctypes_ptr(ws), stream.cuda_stream)
     return {"tissue4096": {"pixels": H * W, "markers": 2000, "conn": 8, "ms": round(ms, 3),
+                           "gpx_s": round(H * W / ms / 1e6, 3), "visits": int(cnt["visits"])}}
+
+
+def run_skiz(args, dev):
+    """Geodesic influence zones on the 4096^2 porous domain (blob field above 8: blobs plus
+    ~70 % of the noisy background), 2000 markers with distinct labels, 8-connectivity.
+    Reports time and Gpixels/s of the whole call (initialisation, propagation, zones)."""
+    import torch
+    from paper_1605_00930_gb300 import iwpp, synth
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    markers, mask = synth.porous_skiz_case()
+    H, W = mask.shape
+    mk = torch.from_numpy(markers.astype(np.int32)).to(dev)
+    m = torch.from_numpy(mask).to(dev)
+    zone = torch.empty((H, W), dtype=torch.int32, device=dev)
+    ws = iwpp.alloc_workspace(iwpp.iwpp_skiz_workspace_bytes(H, W), dev)
+    ts = []
+    for r in range(max(3, args.form_reps) + 1):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = iwpp.iwpp_skiz(ctypes_ptr(mk), ctypes_ptr(m), ctypes_ptr(zone), None, None, H, W, 8,
+                            ctypes_ptr(ws), ws.numel(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise RuntimeError("skiz call failed")
+        if r > 0:
+            ts.append(e0.elapsed_time(e1))
+    if iwpp.iwpp_sync_status(ctypes_ptr(ws), stream.cuda_stream) != 0:
+        raise RuntimeError("skiz device error")
+    ms = float(np.median(ts))
+    cnt = iwpp.iwpp_work_counters(ctypes_ptr(ws), stream.cuda_stream)
+    return {"porous4096": {"pixels": H * W, "markers": 2000, "conn": 8, "ms": round(ms, 3),
                            "gpx_s": round(H * W / ms / 1e6, 3), "visits": int(cnt["visits"])}}
 
 

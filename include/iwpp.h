@@ -407,6 +407,36 @@ IWPP_API int iwpp_watershed(const uint32_t *markers, const void *gradient, int d
                             size_t ws_bytes, void *stream);
 
 /*
+ * Geodesic skeleton by influence zones (SKIZ), as an IWPP propagation on the same tile
+ * engine (one of the operators the paper names as future work for the pattern, Sec. 6).
+ * Domain: pixels where mask != 0 or a marker is set; paths are 4- or 8-connected chains
+ * of domain pixels, a path's length its number of steps. For each domain pixel p, d(p) is
+ * the length of the shortest path from any marker pixel, and L(p) the set of labels of the
+ * marker pixels at that distance. p lies in the influence zone of label l when L(p) = {l},
+ * and on the skeleton when L(p) holds two or more labels. The propagation carries (d, min L,
+ * max L) and merges label sets on equal distances, a join on a distributive lattice: the
+ * result is unique (independent of the order of work) and bit-identical to the definition.
+ *   markers      device, H x W uint32 (4-byte aligned): 0 = none, 1 .. 65534 = label (larger
+ *                labels make the device status IWPP_ERR_ARG)
+ *   mask         device, H x W uint8: non-zero = inside the domain
+ *   zone_out     device, H x W uint32 (4-byte aligned): the label of the pixel's influence
+ *                zone; 0 on the skeleton, outside the domain and where no marker reaches
+ *   dist_out     device, H x W int32 or NULL: d(p), -1 where no marker reaches
+ *   lpair_out    device, H x W uint32 or NULL: (min L << 16) | max L, 0 where unreached
+ *                (the skeleton is where the two halves differ)
+ *   H, W         1 <= H, W and H * W < 2^31 (distances then fit in 31 bits)
+ *   connectivity 4 or 8
+ *   workspace    device, 256-byte aligned, iwpp_skiz_workspace_bytes(H, W) bytes (8 bytes
+ *                of state per pixel plus the tile queue)
+ * Enqueues everything on `stream`; returns IWPP_OK or a host-detected error (device errors
+ * in the workspace status word, see iwpp_sync_status).
+ */
+IWPP_API size_t iwpp_skiz_workspace_bytes(int64_t H, int64_t W);
+IWPP_API int iwpp_skiz(const uint32_t *markers, const uint8_t *mask, uint32_t *zone_out, int32_t *dist_out,
+                       uint32_t *lpair_out, int64_t H, int64_t W, int connectivity, void *workspace,
+                       size_t ws_bytes, void *stream);
+
+/*
  * Euclidean distance transform by wavefront propagation of Voronoi sites (Sec. 3.2,
  * Algorithm 8) on the same persistent tile engine. Background pixels (mask == 0) are
  * their own sites; every other pixel ends with the site, among those its neighbours

@@ -121,6 +121,10 @@ _PROTOS = [
     ("iwpp_watershed", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_skiz_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
+    ("iwpp_skiz", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_size_t, ctypes.c_void_p]),
     ("iwpp_edt_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     ("iwpp_edt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -381,6 +385,39 @@ def watershed(markers, gradient, conn: int = 8, with_levels: bool = False, strea
                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream)), "iwpp_watershed")
     _check(iwpp_sync_status(ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "device")
     return (labels, levels) if with_levels else labels
+
+
+def iwpp_skiz_workspace_bytes(H: int, W: int) -> int:
+    return int(lib().iwpp_skiz_workspace_bytes(H, W))
+
+
+def iwpp_skiz(markers_ptr, mask_ptr, zone_ptr, dist_ptr, lpair_ptr, H, W, conn, ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_skiz(markers_ptr, mask_ptr, zone_ptr, dist_ptr, lpair_ptr, H, W, conn, ws_ptr, ws_bytes,
+                           stream)
+
+
+def skiz(markers, mask, conn: int = 8, with_details: bool = False, stream=None):
+    """Geodesic influence zones of labelled markers (CUDA int32/uint32, 0 = none) inside the
+    domain mask != 0 (CUDA uint8) or marker != 0. Returns the zone labels (int32; 0 on the
+    skeleton and where unreached); with `with_details`, also the distances (int32, -1 where
+    unreached) and the label pairs (min << 16 | max, int32)."""
+    import torch
+    if markers.shape != mask.shape or mask.dtype != torch.uint8:
+        raise ValueError("markers and a uint8 mask of the same shape")
+    H, W = mask.shape
+    dev = mask.device
+    zone = torch.empty((H, W), dtype=torch.int32, device=dev)
+    dist = torch.empty((H, W), dtype=torch.int32, device=dev) if with_details else None
+    lpair = torch.empty((H, W), dtype=torch.int32, device=dev) if with_details else None
+    ws = alloc_workspace(iwpp_skiz_workspace_bytes(H, W), dev)
+    mk, m = markers.contiguous(), mask.contiguous()
+    P = ctypes.c_void_p
+    _check(iwpp_skiz(P(mk.data_ptr()), P(m.data_ptr()), P(zone.data_ptr()),
+                     P(dist.data_ptr()) if dist is not None else None,
+                     P(lpair.data_ptr()) if lpair is not None else None, H, W, int(conn),
+                     P(ws.data_ptr()), ws.numel(), _stream_handle(stream)), "iwpp_skiz")
+    _check(iwpp_sync_status(P(ws.data_ptr()), _stream_handle(stream)), "device")
+    return (zone, dist, lpair) if with_details else zone
 
 
 def iwpp_edt_workspace_bytes(H: int, W: int) -> int:

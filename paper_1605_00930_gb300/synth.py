@@ -135,6 +135,20 @@ def sparse_seed_case(H: int = 16384, W: int = 16384, nblobs: int = 2000, nseeds:
     return Case(seeds_marker(mask, nseeds, rng), mask, 8, "dilate")
 
 
+def porous_skiz_case(H: int = 4096, W: int = 4096, nmarkers: int = 2000, nlabels: int = 2000,
+                     thresh: int = 8, image_idx: int = 0):
+    """Influence-zone input: the domain is the tissue-like blob field above a low threshold
+    (every blob plus ~70 % of the noisy background: a percolating porous region); markers
+    are `nmarkers` uniform pixels with labels uniform in 1..nlabels. Returns (markers uint32,
+    domain mask uint8)."""
+    rng = rng_for(10, image_idx)
+    field = blob_field_u8(H, W, blob_count(H, W), rng)
+    mask = (field > thresh).astype(np.uint8)
+    markers = np.zeros((H, W), np.uint32)
+    markers[rng.integers(0, H, nmarkers), rng.integers(0, W, nmarkers)] = rng.integers(1, nlabels + 1, nmarkers)
+    return markers, mask
+
+
 def mixed_batch(n: int = 256, workload_id: int = 4, min_side: int = 256, max_side: int = 4096,
                 conn: int = 8) -> list[Case]:
     """Uneven batch: log-uniform sides, u8/u16 with p = 1/2; the first half are

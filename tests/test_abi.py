@@ -127,6 +127,25 @@ def test_watershed_and_operator_host_errors(iwpp):
     assert iwpp.iwpp_regional_maxima(P(a16), P(a16), null, 4, 4, 8, 0, P(ws), 4096, null) == 1
 
 
+def test_skiz_host_errors(iwpp):
+    buf = (ctypes.c_uint8 * 4096)()
+    a = ctypes.addressof(buf)
+    a16 = (a + 15) // 16 * 16
+    ws = (a + 255) // 256 * 256 if a % 256 else a
+    P, null = ctypes.c_void_p, ctypes.c_void_p(0)
+    assert iwpp.iwpp_skiz_workspace_bytes(0, 4) == 0 and iwpp.iwpp_skiz_workspace_bytes(1 << 16, 1 << 15) == 0
+    assert iwpp.iwpp_skiz_workspace_bytes(64, 64) >= 64 * 64 * 8
+    assert iwpp.iwpp_skiz(null, P(a16), P(a16), null, null, 4, 4, 8, P(ws), 4096, null) == 1      # no markers
+    assert iwpp.iwpp_skiz(P(a16), null, P(a16), null, null, 4, 4, 8, P(ws), 4096, null) == 1      # no mask
+    assert iwpp.iwpp_skiz(P(a16), P(a16), null, null, null, 4, 4, 8, P(ws), 4096, null) == 1      # no output
+    assert iwpp.iwpp_skiz(P(a16), P(a16), P(a16), null, null, 4, 4, 6, P(ws), 4096, null) == 1    # connectivity
+    assert iwpp.iwpp_skiz(P(a16), P(a16), P(a16 + 2), null, null, 4, 4, 8, P(ws), 4096, null) == 1
+    assert iwpp.iwpp_skiz(P(a16), P(a16), P(a16), P(a16 + 1), null, 4, 4, 8, P(ws), 4096, null) == 1
+    assert iwpp.iwpp_skiz(P(a16), P(a16), P(a16), null, null, 1 << 16, 1 << 15, 8, P(ws), 4096, null) == 1
+    assert iwpp.iwpp_skiz(P(a16), P(a16), P(a16), null, null, 4, 4, 8, null, 4096, null) == 3
+    assert iwpp.iwpp_skiz(P(a16), P(a16), P(a16), null, null, 4, 4, 8, P(ws), 64, null) == 3
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     import importlib
     from paper_1605_00930_gb300 import iwpp as m

@@ -95,7 +95,7 @@ typedef enum {
  *                      its next tile from the highest level that has one (the
  *                      level of a queued tile is the value the notification
  *                      that queued it can raise it to; the tile-granular form of
- *                      Sec. 3.2's heap-ordered propagation). Register solver,
+ *                      Sec. 4.4's heap-ordered propagation). Register solver,
  *                      single-image calls only
  *   watchdog_ns        the persistent kernel gives up with IWPP_ERR_TIMEOUT
  *                      when a wait for work lasts longer than this
@@ -380,6 +380,31 @@ IWPP_API int iwpp_hdome(const void *image, void *out, int64_t H, int64_t W, uint
                         int dtype, void *workspace, size_t ws_bytes, void *stream);
 IWPP_API int iwpp_regional_maxima(const void *image, void *scratch, uint8_t *out, int64_t H, int64_t W,
                                   int connectivity, int dtype, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Reconstruction of an image held in HOST memory, band by band (images larger than the
+ * device's memory; Sec. 1 cites 100K x 100K scans, Sec. 4.5 splits such images into tasks
+ * and corrects the propagation across task borders). The image is cut into horizontal bands
+ * of band_rows rows. Each band is copied to the device with one halo row above and below
+ * whose mask is set to their marker (fixed sources), reconstructed through the single-image
+ * path, and copied back. Bands are visited top to bottom, then bottom to top, a band again
+ * only after a neighbour band changed, until no band is left to visit: the result is
+ * bit-identical to iwpp_reconstruct. Blocking: the call synchronises `stream` after every
+ * band.
+ *   marker_inout, mask   HOST, H x W of `dtype`, row-major (pinned memory copies fastest);
+ *                        the result overwrites marker_inout
+ *   band_rows            rows per band, >= 1 (a band of >= H rows is one reconstruction)
+ *   workspace            device, 256-byte aligned, iwpp_host_workspace_bytes(H, W, dtype,
+ *                        band_rows) bytes: two (band_rows + 2) x W planes, one band_rows x W
+ *                        plane and a single-image workspace for band_rows + 2 rows
+ *   visits_out           host int32 or NULL: band reconstructions made
+ * Returns IWPP_OK, a host-detected error, or the first device error of any band (e.g.
+ * IWPP_ERR_PRECONDITION; the host image is then unspecified).
+ */
+IWPP_API size_t iwpp_host_workspace_bytes(int64_t H, int64_t W, int dtype, int64_t band_rows);
+IWPP_API int iwpp_reconstruct_host(void *marker_inout, const void *mask, int64_t H, int64_t W, int connectivity,
+                                   int op, int dtype, int64_t band_rows, void *workspace, size_t ws_bytes,
+                                   void *stream, int32_t *visits_out);
 
 /*
  * Marker-controlled watershed by flooding, as an IWPP propagation on the same tile engine

@@ -171,7 +171,7 @@ __device__ inline bool push_tile(const EngineArgs &a, uint32_t t) {
     return true;
 }
 
-// ---- value-ordered tile queue (Sec. 3.2's heap-based propagation, at tile granularity) ---
+// ---- value-ordered tile queue (Sec. 4.4's heap-based propagation, at tile granularity) ---
 // One ticketed ring per value level. A push publishes its entry and then counts it in
 // `avail`; a pop first claims one published entry of the highest level that has one (an
 // atomic decrement that it undoes if it lost the race for the last entry), then takes a

@@ -121,6 +121,11 @@ _PROTOS = [
     ("iwpp_watershed", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_host_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64]),
+    ("iwpp_reconstruct_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_int32)]),
     ("iwpp_skiz_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     ("iwpp_skiz", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
@@ -385,6 +390,44 @@ def watershed(markers, gradient, conn: int = 8, with_levels: bool = False, strea
                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream)), "iwpp_watershed")
     _check(iwpp_sync_status(ctypes.c_void_p(ws.data_ptr()), _stream_handle(stream)), "device")
     return (labels, levels) if with_levels else labels
+
+
+def iwpp_host_workspace_bytes(H: int, W: int, dtype: int, band_rows: int) -> int:
+    return int(lib().iwpp_host_workspace_bytes(H, W, dtype, band_rows))
+
+
+def iwpp_reconstruct_host(marker_ptr, mask_ptr, H, W, conn, op, dtype, band_rows, ws_ptr, ws_bytes, stream,
+                          visits_ref=None) -> int:
+    return lib().iwpp_reconstruct_host(marker_ptr, mask_ptr, H, W, conn, op, dtype, band_rows, ws_ptr, ws_bytes,
+                                       stream, visits_ref)
+
+
+class HostReconstructor:
+    """Reconstruction of images in host memory, band by band (iwpp_reconstruct_host): holds
+    the device workspace for H x W images of one dtype and band height."""
+
+    def __init__(self, H: int, W: int, dtype, band_rows: int, device=None):
+        import torch
+        self.H, self.W, self.band_rows = int(H), int(W), int(band_rows)
+        self.dtype_code = {torch.uint8: IWPP_U8, torch.uint16: IWPP_U16}[dtype]
+        nbytes = iwpp_host_workspace_bytes(self.H, self.W, self.dtype_code, self.band_rows)
+        if nbytes == 0:
+            raise ValueError("unsupported size or band height")
+        self.ws = alloc_workspace(nbytes, device)
+        self.band_visits = 0
+
+    def __call__(self, marker, mask, conn: int = 8, op: str = "dilate", stream=None) -> int:
+        """marker, mask: contiguous CPU tensors (pinned for speed); marker is overwritten.
+        Returns the status (0 = IWPP_OK)."""
+        if marker.is_cuda or mask.is_cuda or not marker.is_contiguous() or not mask.is_contiguous():
+            raise ValueError("contiguous host tensors expected")
+        r = ctypes.c_int32(0)
+        rc = iwpp_reconstruct_host(ctypes.c_void_p(marker.data_ptr()), ctypes.c_void_p(mask.data_ptr()), self.H,
+                                   self.W, int(conn), OPS[op], self.dtype_code, self.band_rows,
+                                   ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), _stream_handle(stream),
+                                   ctypes.byref(r))
+        self.band_visits = int(r.value)
+        return rc
 
 
 def iwpp_skiz_workspace_bytes(H: int, W: int) -> int:

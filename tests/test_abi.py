@@ -146,6 +146,23 @@ def test_skiz_host_errors(iwpp):
     assert iwpp.iwpp_skiz(P(a16), P(a16), P(a16), null, null, 4, 4, 8, P(ws), 64, null) == 3
 
 
+def test_host_band_errors(iwpp):
+    buf = (ctypes.c_uint8 * 4096)()
+    a = ctypes.addressof(buf)
+    ws = (a + 255) // 256 * 256 if a % 256 else a
+    P, null = ctypes.c_void_p, ctypes.c_void_p(0)
+    f = iwpp.iwpp_reconstruct_host
+    assert iwpp.iwpp_host_workspace_bytes(0, 4, 0, 4) == 0 and iwpp.iwpp_host_workspace_bytes(4, 4, 0, 0) == 0
+    assert iwpp.iwpp_host_workspace_bytes(4, 4, 2, 4) == 0
+    assert f(null, P(a), 4, 4, 8, 0, 0, 2, P(ws), 4096, null, None) == 1          # no marker
+    assert f(P(a), null, 4, 4, 8, 0, 0, 2, P(ws), 4096, null, None) == 1          # no mask
+    assert f(P(a), P(a), 4, 4, 5, 0, 0, 2, P(ws), 4096, null, None) == 1          # connectivity
+    assert f(P(a), P(a), 4, 4, 8, 2, 0, 2, P(ws), 4096, null, None) == 1          # op
+    assert f(P(a), P(a), 4, 4, 8, 0, 3, 2, P(ws), 4096, null, None) == 1          # dtype
+    assert f(P(a), P(a), 4, 4, 8, 0, 0, 0, P(ws), 4096, null, None) == 1          # band height
+    assert f(P(a), P(a), 0, 4, 8, 0, 0, 2, P(ws), 4096, null, None) == 1          # size
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     import importlib
     from paper_1605_00930_gb300 import iwpp as m

@@ -113,7 +113,8 @@ class ClockSampler:
 # ncu traffic record: a change to any of them makes the record stale).
 KERNEL_SOURCES = ["paper_1605_00930_gb300/csrc/iwpp_api.cu",
                   "paper_1605_00930_gb300/csrc/iwpp_engine.cuh", "paper_1605_00930_gb300/csrc/iwpp_host.h",
-                  "paper_1605_00930_gb300/csrc/iwpp_kern_reg.cu", "paper_1605_00930_gb300/csrc/iwpp_regtile.cuh"]
+                  "paper_1605_00930_gb300/csrc/iwpp_kern_reg.cu", "paper_1605_00930_gb300/csrc/iwpp_regtile.cuh",
+                  "paper_1605_00930_gb300/csrc/iwpp_kern_coop.cu", "paper_1605_00930_gb300/csrc/iwpp_coop.cuh"]
 
 
 def kernel_digest() -> str:
@@ -274,8 +275,9 @@ def run_ours(args, rank: int, world: int):
     s = bytes_per_px[0]
     nl = len(dev_cases)
     plan = iwpp.iwpp_default_plan()
-    reg = plan.local_solver == iwpp.IWPP_SOLVER_REGISTER
-    drain_name, scan_name = ("drain_reg_kernel", "scan_reg_kernel") if reg else ("drain_kernel", "scan_kernel")
+    drain_name, scan_name = {iwpp.IWPP_SOLVER_QUEUE: ("drain_kernel", "scan_kernel"),
+                             iwpp.IWPP_SOLVER_REGISTER: ("drain_reg_kernel", "scan_reg_kernel"),
+                             iwpp.IWPP_SOLVER_COOP: ("drain_coop_kernel", "scan_coop_kernel")}[plan.local_solver]
     dominant = drain_name if drain_ms >= scan_ms else scan_name
     dom_ms = (drain_ms if dominant == drain_name else scan_ms) / (args.steps * nl)
     alg_bytes = 3 * s * cases[0][1].size   # compulsory bytes of one reconstruction: read J, I, write J
@@ -625,7 +627,7 @@ def run_forms(args, dev):
         ref = [m.cpu().numpy() for m, _, _, _ in items]
         res["plain_ms"] = round(ms, 3)
         res["plain_gpx_s"] = round(px / ms / 1e6, 3)
-        plan = iwpp.iwpp_default_plan()
+        plan = iwpp.iwpp_default_batch_plan()
         if tune:
             for (m, _, _, _), m0 in zip(items, init):   # tune on the inputs, not on the result
                 m.copy_(m0)

@@ -89,7 +89,13 @@ typedef enum {
  *                      IWPP_SOLVER_REGISTER, the tile held in registers (two
  *                      columns per lane) and swept down and up until no pixel
  *                      changes (Algorithm 1's update in Gauss-Seidel order);
- *                      the register solver needs tile_w == 64, tile_h <= 16
+ *                      the register solver needs tile_w == 64, tile_h <= 16;
+ *                      or IWPP_SOLVER_COOP, one CTA per 64 x 64 tile: each of
+ *                      its four warps holds a 16-row strip as the register
+ *                      solver does, and the strips exchange their boundary
+ *                      rows through shared memory until the tile is settled
+ *                      (tile_h == tile_w == 64, no sweeps, no value levels,
+ *                      at most 4 CTAs per SM, single-image calls only)
  *   value_levels       0 or 1: the persistent kernel's tile queue is one FIFO;
  *                      2..16: one queue per value level, and a worker takes
  *                      its next tile from the highest level that has one (the
@@ -113,10 +119,15 @@ typedef struct {
 } iwpp_plan;
 
 /* Values of iwpp_plan.local_solver. */
-enum { IWPP_SOLVER_QUEUE = 0, IWPP_SOLVER_REGISTER = 1 };
+enum { IWPP_SOLVER_QUEUE = 0, IWPP_SOLVER_REGISTER = 1, IWPP_SOLVER_COOP = 2 };
 
-/* Fills *plan with the static default schedule. Returns IWPP_OK. */
+/* Fills *plan with the static default schedule of single-image calls (a NULL plan there):
+ * 64 x 64 tiles, cooperative solver. Returns IWPP_OK. */
 IWPP_API int iwpp_default_plan(iwpp_plan *plan);
+
+/* Fills *plan with the static default schedule of batch calls (a NULL plan there): 16 x 64
+ * tiles, register solver. Returns IWPP_OK. */
+IWPP_API int iwpp_default_batch_plan(iwpp_plan *plan);
 
 /* 1 if (tile_h, tile_w) is a compiled tile shape, else 0. */
 IWPP_API int iwpp_tile_shape_supported(int32_t tile_h, int32_t tile_w);

@@ -45,6 +45,7 @@ struct KernelSet {
     void (*drain)(EngineArgs);
     size_t (*smem)(uint32_t);
     RegKernelSet reg;                // register local solver (16 x 64 tiles), else null
+    RegKernelSet coop;               // cooperative local solver (64 x 64 tiles), else null
 };
 static constexpr int kMixed = 4;
 
@@ -55,6 +56,7 @@ static KernelSet make_set() {
     k.drain = drain_kernel<T, CONN, TH, TW>;
     k.smem = &Tile<T, CONN, TH, TW>::smem_bytes;
     k.reg = reg_kernel_set(TH, TW, (sizeof(T) == 2 ? 1 : 0) | (CONN == 8 ? 2 : 0));
+    k.coop = coop_kernel_set(TH, TW, (sizeof(T) == 2 ? 1 : 0) | (CONN == 8 ? 2 : 0));
     return k;
 }
 
@@ -73,6 +75,7 @@ static void fill_shape(KernelSet (&row)[5]) {
     row[kMixed].drain = drain_mixed_kernel<TH, TW>;
     row[kMixed].smem = &mixed_smem_bytes<TH, TW>;
     row[kMixed].reg = reg_kernel_set(TH, TW, kMixed);
+    row[kMixed].coop = coop_kernel_set(TH, TW, kMixed);
 }
 
 static KernelSet g_sets[kNumShapes][5];
@@ -107,7 +110,7 @@ static cudaError_t ensure_smem_attr(int shape, int v, size_t bytes) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute((const void *)k.drain, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     if (e != cudaSuccess) return e;
-    for (void (*f)(EngineArgs) : {k.reg.scan, k.reg.drain, k.reg.drain_hi}) {
+    for (void (*f)(EngineArgs) : {k.reg.scan, k.reg.drain, k.reg.drain_hi, k.coop.scan, k.coop.drain}) {
         if (!f) continue;
         e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e != cudaSuccess) return e;
@@ -129,16 +132,21 @@ int device_sm_count() {
 // shared memory. Register plans asking for more than kRegBlocks CTAs per SM get the
 // high-occupancy build of the persistent kernel.
 static void (*drain_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
+    if (p.local_solver == IWPP_SOLVER_COOP) return k.coop.drain;
     if (p.local_solver != IWPP_SOLVER_REGISTER) return k.drain;
     return p.blocks_per_sm > kRegBlocks ? k.reg.drain_hi : k.reg.drain;
 }
 static void (*scan_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
+    if (p.local_solver == IWPP_SOLVER_COOP) return k.coop.scan;
     return p.local_solver == IWPP_SOLVER_REGISTER ? k.reg.scan : k.scan;
 }
 static size_t drain_smem(const iwpp_plan &p, const KernelSet &k) {
+    if (p.local_solver == IWPP_SOLVER_COOP) return k.coop.smem((uint32_t)p.smem_queue_cap);
     return p.local_solver == IWPP_SOLVER_REGISTER ? k.reg.smem((uint32_t)p.smem_queue_cap)
                                                   : k.smem((uint32_t)p.smem_queue_cap);
 }
+// Tiles one persistent CTA works on at a time: one per warp, or one per CTA (cooperative).
+static int tiles_per_cta(const iwpp_plan &p) { return p.local_solver == IWPP_SOLVER_COOP ? 1 : kWarpsPerCta; }
 
 // Persistent CTAs for a plan: blocks_per_sm (or the occupancy maximum) x SMs, never more
 // CTAs than needed to give every tile its own warp.
@@ -155,7 +163,7 @@ static int drain_grid(const iwpp_plan &p, int v, uint32_t ntiles) {
     }
     const int sms = device_sm_count();
     long long g = (long long)bps * sms;
-    const long long need = ((long long)ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    const long long need = ((long long)ntiles + tiles_per_cta(p) - 1) / tiles_per_cta(p);
     if (g > need) g = need;
     return g < 1 ? 1 : (int)g;
 }
@@ -167,17 +175,24 @@ bool plan_valid(const iwpp_plan &p) {
     if (p.smem_queue_cap < 16 || p.smem_queue_cap > p.tile_h * p.tile_w) return false;
     if (p.blocks_per_sm < 0 || p.blocks_per_sm > 32) return false;
     if (p.watchdog_ns < 0) return false;
-    if (p.local_solver != IWPP_SOLVER_QUEUE && p.local_solver != IWPP_SOLVER_REGISTER) return false;
+    if (p.local_solver != IWPP_SOLVER_QUEUE && p.local_solver != IWPP_SOLVER_REGISTER &&
+        p.local_solver != IWPP_SOLVER_COOP)
+        return false;
+    if (p.local_solver == IWPP_SOLVER_COOP &&
+        (!coop_kernel_set(p.tile_h, p.tile_w, 0).drain || p.value_levels > 1 || p.blocks_per_sm > kRegBlocks ||
+         p.sweeps != 0 || p.revisit_sweeps != 0))
+        return false;
     if (p.local_solver == IWPP_SOLVER_REGISTER && !reg_kernel_set(p.tile_h, p.tile_w, 0).drain) return false;
     if (p.value_levels < 0 || p.value_levels > kMaxLevels) return false;
     if (p.value_levels > 1 && p.local_solver != IWPP_SOLVER_REGISTER) return false;
     return true;
 }
 
-// The measured best static plan: 16 x 64 tiles settled by the register solver, no sweeps
-// before the persistent kernel (the scan kernel still checks the precondition and
-// collects the frontier).
-void default_plan(iwpp_plan *p) {
+// The measured best static plans. Batches: 16 x 64 tiles settled by the register solver
+// (one tile per warp), no sweeps before the persistent kernel (the scan kernel still checks
+// the precondition and collects the frontier). Single images: 64 x 64 tiles settled by the
+// cooperative solver (one tile per CTA of four warps).
+void default_batch_plan(iwpp_plan *p) {
     p->tile_h = 16;
     p->tile_w = 64;
     p->sweeps = 0;
@@ -187,6 +202,13 @@ void default_plan(iwpp_plan *p) {
     p->local_solver = IWPP_SOLVER_REGISTER;
     p->value_levels = 0;
     p->watchdog_ns = 0;
+}
+
+void default_plan(iwpp_plan *p) {
+    default_batch_plan(p);
+    p->tile_h = 64;
+    p->tile_w = 64;
+    p->local_solver = IWPP_SOLVER_COOP;
 }
 
 // Pixel offsets are 64-bit everywhere; sides stay below 2^31 (ints in the kernels) and
@@ -250,7 +272,8 @@ static bool make_layout(int64_t H, int64_t W, int v, const iwpp_plan &p, Layout 
     L.ntiles = (uint32_t)(tx * ty);
     L.grid = drain_grid(p, v, L.ntiles);
     if (L.grid <= 0) return false;
-    L.ovcap = (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap);
+    // per-warp overflow queues: the queue solver's only
+    L.ovcap = p.local_solver == IWPP_SOLVER_QUEUE ? (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap) : 0u;
     L.nlevels = p.value_levels > 1 ? (uint32_t)p.value_levels : 1u;
     L.state = 256;
     L.lvl = L.state + align256((size_t)L.ntiles * 4);
@@ -367,7 +390,7 @@ static bool make_batch_layout(const iwpp_image *imgs, int n, const iwpp_plan &p,
     L.ntiles = (uint32_t)nt;
     L.grid = drain_grid(p, batch_variant(imgs, n), L.ntiles);
     if (L.grid <= 0) return false;
-    L.ovcap = (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap);
+    L.ovcap = p.local_solver == IWPP_SOLVER_QUEUE ? (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap) : 0u;
     L.table = 256;
     L.state = L.table + align256((size_t)n * sizeof(ImageView));
     L.queue = L.state + align256((size_t)L.ntiles * 4);
@@ -378,7 +401,7 @@ static bool make_batch_layout(const iwpp_image *imgs, int n, const iwpp_plan &p,
 
 size_t batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan_in) {
     iwpp_plan p;
-    if (plan_in) p = *plan_in; else default_plan(&p);
+    if (plan_in) p = *plan_in; else default_batch_plan(&p);
     if (!plan_valid(p)) return 0;
     BatchLayout L;
     if (!make_batch_layout(imgs, n, p, L, nullptr)) return 0;
@@ -389,8 +412,9 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
                       const uint8_t *tile_sweeps, uint32_t *tile_work, void *ws, size_t ws_bytes,
                       cudaStream_t stream) {
     iwpp_plan p;
-    if (plan_in) p = *plan_in; else default_plan(&p);
-    if (!plan_valid(p) || p.value_levels > 1) return IWPP_ERR_ARG;   // batches: one FIFO
+    if (plan_in) p = *plan_in; else default_batch_plan(&p);
+    if (!plan_valid(p) || p.value_levels > 1 || p.local_solver == IWPP_SOLVER_COOP)
+        return IWPP_ERR_ARG;   // batches: one FIFO, one tile per warp
     if (!imgs || n < 1) return IWPP_ERR_ARG;
     for (int i = 0; i < n; i++)
         if (check_image(imgs[i]) != IWPP_OK) return IWPP_ERR_ARG;
@@ -453,6 +477,12 @@ extern "C" int iwpp_default_plan(iwpp_plan *plan) {
     return IWPP_OK;
 }
 
+extern "C" int iwpp_default_batch_plan(iwpp_plan *plan) {
+    if (!plan) return IWPP_ERR_ARG;
+    iwpp::default_batch_plan(plan);
+    return IWPP_OK;
+}
+
 extern "C" int iwpp_tile_shape_supported(int32_t tile_h, int32_t tile_w) {
     return iwpp::shape_index(tile_h, tile_w) >= 0 ? 1 : 0;
 }
@@ -491,7 +521,7 @@ extern "C" int iwpp_drain(void *marker_inout, const void *mask, int64_t H, int64
 
 extern "C" int64_t iwpp_batch_tile_count(const iwpp_image *imgs, int n, const iwpp_plan *plan) {
     iwpp_plan p;
-    if (plan) p = *plan; else iwpp::default_plan(&p);
+    if (plan) p = *plan; else iwpp::default_batch_plan(&p);
     if (!iwpp::plan_valid(p)) return -1;
     return iwpp::batch_tiles(imgs, n, p, nullptr);
 }

@@ -23,10 +23,12 @@ struct RegKernelSet {
 };
 constexpr int kRegBlocks = 4, kRegHiBlocks = 6;
 RegKernelSet reg_kernel_set(int th, int tw, int v);
+RegKernelSet coop_kernel_set(int th, int tw, int v);   // cooperative solver (64 x 64 tiles)
 
 int shape_index(int th, int tw);
 bool plan_valid(const iwpp_plan &p);
-void default_plan(iwpp_plan *p);
+void default_plan(iwpp_plan *p);         // single images
+void default_batch_plan(iwpp_plan *p);   // batches
 size_t align256(size_t x);
 int device_sm_count();
 int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int conn, int op, int dtype,

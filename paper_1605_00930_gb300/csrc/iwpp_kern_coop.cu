@@ -1,0 +1,30 @@
+// iwpp_kern_coop.cu — instantiations of the cooperative local solver's kernels (one
+// translation unit of their own, compiled in parallel with the others).
+#include "iwpp_host.h"
+#include "iwpp_coop.cuh"
+
+namespace iwpp {
+
+template <typename T, int CONN>
+static RegKernelSet coop_set() {
+    RegKernelSet k;
+    k.scan = scan_coop_kernel<T, CONN>;
+    k.drain = drain_coop_kernel<T, CONN>;
+    k.drain_hi = nullptr;   // one build: 4 CTAs of 4 warps per SM
+    k.smem = &coop_smem_fn<T, CONN>;
+    return k;
+}
+
+RegKernelSet coop_kernel_set(int th, int tw, int v) {
+    RegKernelSet none = {nullptr, nullptr, nullptr, nullptr};
+    if (th != kCoopRows || tw != RegTile<uint8_t, 8, kCoopStrip>::TW) return none;
+    switch (v) {
+        case 0: return coop_set<uint8_t, 4>();
+        case 1: return coop_set<uint16_t, 4>();
+        case 2: return coop_set<uint8_t, 8>();
+        case 3: return coop_set<uint16_t, 8>();
+        default: return none;   // single-image kinds only
+    }
+}
+
+}  // namespace iwpp

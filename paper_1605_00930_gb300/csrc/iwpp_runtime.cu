@@ -189,7 +189,7 @@ static void cache_store(const char *path, const std::string &key, const iwpp_pla
 int autotune(const iwpp_image *imgs, int n, iwpp_plan *plan, int reps, const char *cache_path,
              cudaStream_t stream, float *best_ms) {
     if (!imgs || n < 1 || !plan) return IWPP_ERR_ARG;
-    if (!plan_valid(*plan)) return IWPP_ERR_ARG;
+    if (!plan_valid(*plan) || plan->local_solver == IWPP_SOLVER_COOP) return IWPP_ERR_ARG;   // batches only
     for (int i = 0; i < n; i++)
         if (batch_tiles(imgs + i, 1, *plan, nullptr) < 1) return IWPP_ERR_ARG;
     const std::string key = cache_key(imgs, n);

@@ -557,7 +557,7 @@ static int schedule_impl(const iwpp_image *imgs, int n, const iwpp_plan *plan_in
                          const float *preds_in, float *feats_out, uint32_t *order, uint8_t *sweeps, void *sws,
                          size_t sws_bytes, cudaStream_t stream, int phases) {
     iwpp_plan p;
-    if (plan_in) p = *plan_in; else default_plan(&p);
+    if (plan_in) p = *plan_in; else default_batch_plan(&p);
     if (!plan_valid(p) || !sws || ((uintptr_t)sws & 255)) return IWPP_ERR_ARG;
     for (int i = 0; i < n; i++)
         if (!imgs || batch_tiles(imgs + i, 1, p, nullptr) < 1) return IWPP_ERR_ARG;
@@ -599,7 +599,7 @@ extern "C" int64_t iwpp_batch_block_count(const iwpp_image *imgs, int n) {
 
 extern "C" size_t iwpp_sched_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan) {
     iwpp_plan p;
-    if (plan) p = *plan; else iwpp::default_plan(&p);
+    if (plan) p = *plan; else iwpp::default_batch_plan(&p);
     if (!iwpp::plan_valid(p)) return 0;
     iwpp::SchedLayout L;
     return iwpp::sched_layout(imgs, n, p, L, nullptr, nullptr) ? L.total : 0;
@@ -664,7 +664,7 @@ extern "C" int iwpp_tile_work_to_blocks(const iwpp_image *imgs, int n, const iwp
                                         const uint32_t *tile_work, unsigned long long *block_work, void *sched_ws,
                                         size_t sws_bytes, void *stream) {
     iwpp_plan p;
-    if (plan) p = *plan; else iwpp::default_plan(&p);
+    if (plan) p = *plan; else iwpp::default_batch_plan(&p);
     if (!iwpp::plan_valid(p) || !tile_work || !block_work || !sched_ws) return IWPP_ERR_ARG;
     std::vector<uint32_t> bb, tb;
     iwpp::SchedLayout L;

@@ -19,7 +19,7 @@ IWPP_DILATE, IWPP_ERODE = 0, 1
 STATUS = {0: "IWPP_OK", 1: "IWPP_ERR_ARG", 2: "IWPP_ERR_PRECONDITION", 3: "IWPP_ERR_WORKSPACE",
           4: "IWPP_ERR_QUEUE_FULL", 5: "IWPP_ERR_TIMEOUT", 6: "IWPP_ERR_CUDA", 7: "IWPP_ERR_INTERNAL"}
 OPS = {"dilate": IWPP_DILATE, "erode": IWPP_ERODE}
-IWPP_SOLVER_QUEUE, IWPP_SOLVER_REGISTER = 0, 1
+IWPP_SOLVER_QUEUE, IWPP_SOLVER_REGISTER, IWPP_SOLVER_COOP = 0, 1, 2
 
 
 class IwppError(RuntimeError):
@@ -54,6 +54,7 @@ _lock = threading.Lock()
 # (name, restype, argtypes) of every exported C function
 _PROTOS = [
     ("iwpp_default_plan", ctypes.c_int, [ctypes.POINTER(Plan)]),
+    ("iwpp_default_batch_plan", ctypes.c_int, [ctypes.POINTER(Plan)]),
     ("iwpp_tile_shape_supported", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     ("iwpp_workspace_bytes", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                                ctypes.POINTER(Plan)]),
@@ -163,8 +164,16 @@ def exported_symbols():
 # ---- thin wrappers with the C names ----------------------------------------------------
 
 def iwpp_default_plan() -> Plan:
+    """Default plan of single-image calls (64 x 64 tiles, cooperative solver)."""
     p = Plan()
     lib().iwpp_default_plan(ctypes.byref(p))
+    return p
+
+
+def iwpp_default_batch_plan() -> Plan:
+    """Default plan of batch calls (16 x 64 tiles, register solver)."""
+    p = Plan()
+    lib().iwpp_default_batch_plan(ctypes.byref(p))
     return p
 
 
@@ -569,43 +578,6 @@ class Reconstructor:
     def counters(self, stream=None):
         return iwpp_work_counters(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))
 
-    def graph(self, order=None, sweeps=None) -> "Graph":
-        """Capture this batch (with an optional device schedule) into a CUDA graph."""
-        g = iwpp_batch_graph_create(self.descs, self.plan, _ptr(order), _ptr(sweeps),
-                                    ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel())
-        return Graph(g, (order, sweeps))
-
-    def autotune(self, reps: int = 2, cache_path: str | None = None, stream=None):
-        """Pick this batch's plan with the library's autotuner (markers are restored). The
-        workspace is re-sized for the chosen plan."""
-        plan = Plan.from_buffer_copy(self.plan) if self.plan is not None else iwpp_default_plan()
-        plan, ms = iwpp_autotune_batch(self.descs, plan, reps, cache_path, _stream_handle(stream))
-        self.plan = plan
-        self.ntiles = iwpp_batch_tile_count(self.descs, plan)
-        nbytes = iwpp_batch_workspace_bytes(self.descs, plan)
-        if nbytes > self.ws.numel():
-            self.ws = alloc_workspace(nbytes, self.ws.device)
-        return plan, ms
-
-
-class Graph:
-    """An executable CUDA graph of one batch call (see iwpp_batch_graph_create)."""
-
-    def __init__(self, handle, keepalive):
-        self.handle = handle
-        self._keep = keepalive
-
-    def launch(self, stream=None) -> int:
-        return iwpp_graph_launch(self.handle, _stream_handle(stream))
-
-    def __del__(self):
-        if getattr(self, "handle", None):
-            try:
-                iwpp_graph_destroy(self.handle)
-            except Exception:
-                pass
-            self.handle = None
-
 
 def reconstruct(marker, mask, conn: int = 8, op: str = "dilate", plan: Plan | None = None, stream=None):
     """Reconstruct ``mask`` from ``marker`` in place on ``marker`` (torch CUDA tensors,
@@ -673,7 +645,7 @@ class Batch:
     def autotune(self, reps: int = 2, cache_path: str | None = None, stream=None):
         """Pick this batch's plan with the library's autotuner (markers are restored). The
         workspace is re-sized for the chosen plan."""
-        plan = Plan.from_buffer_copy(self.plan) if self.plan is not None else iwpp_default_plan()
+        plan = Plan.from_buffer_copy(self.plan) if self.plan is not None else iwpp_default_batch_plan()
         plan, ms = iwpp_autotune_batch(self.descs, plan, reps, cache_path, _stream_handle(stream))
         self.plan = plan
         self.ntiles = iwpp_batch_tile_count(self.descs, plan)

@@ -86,7 +86,7 @@ def block_labels(items, plan=None, options=SWEEP_OPTIONS, reps: int = 1):
     nb = iwpp.iwpp_batch_block_count(B.descs)
     sws = iwpp.alloc_workspace(iwpp.iwpp_sched_workspace_bytes(B.descs, plan), init[0].device)
     cycles = np.zeros((len(options), nb))
-    own = (plan if plan is not None else iwpp.iwpp_default_plan()).sweeps
+    own = (plan if plan is not None else iwpp.iwpp_default_batch_plan()).sweeps
     for oi, s in enumerate(options):
         for _ in range(reps):
             for (m, _, _, _), m0 in zip(items, init):

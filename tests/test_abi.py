@@ -48,6 +48,10 @@ def test_default_plan_and_shapes(iwpp):
     p = iwpp.iwpp_default_plan()
     assert iwpp.iwpp_tile_shape_supported(p.tile_h, p.tile_w)
     assert p.sweeps >= 0 and 16 <= p.smem_queue_cap <= p.tile_h * p.tile_w
+    assert (p.tile_h, p.tile_w, p.local_solver) == (64, 64, iwpp.IWPP_SOLVER_COOP)
+    b = iwpp.iwpp_default_batch_plan()
+    assert (b.tile_h, b.tile_w, b.local_solver) == (16, 64, iwpp.IWPP_SOLVER_REGISTER)
+    assert iwpp.iwpp_tile_shape_supported(b.tile_h, b.tile_w)
     for shape in [(32, 32), (32, 64), (64, 64), (16, 32), (16, 64)]:
         assert iwpp.iwpp_tile_shape_supported(*shape)
     assert not iwpp.iwpp_tile_shape_supported(48, 48)
@@ -80,11 +84,19 @@ def test_host_argument_errors_return_before_any_launch(iwpp):
     assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
     # the register solver needs 16 x 64 tiles; unknown solvers, value levels beyond 16 and
     # value levels with the queue solver are rejected
-    for th, tw, solver, levels in [(32, 32, 1, 0), (32, 64, 1, 0), (16, 64, 2, 0), (16, 64, 1, 17),
-                                   (16, 64, 0, 4), (16, 64, 1, -1)]:
+    for th, tw, solver, levels in [(32, 32, 1, 0), (32, 64, 1, 0), (16, 64, 3, 0), (16, 64, 1, 17),
+                                   (16, 64, 0, 4), (16, 64, 1, -1), (16, 64, 2, 0), (32, 64, 2, 0),
+                                   (64, 64, 2, 4)]:
         p = iwpp.iwpp_default_plan()
         p.tile_h, p.tile_w, p.local_solver, p.value_levels = th, tw, solver, levels
         assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
+    # the cooperative solver takes no sweeps and at most 4 CTAs per SM
+    for kw in [{"sweeps": 1}, {"revisit_sweeps": 2}, {"blocks_per_sm": 6}]:
+        p = iwpp.iwpp_default_plan()
+        p.tile_h, p.tile_w, p.local_solver = 64, 64, 2
+        for k, v in kw.items():
+            setattr(p, k, v)
+        assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1, kw
     # missing / misaligned workspace
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, null, 16, null) == 3
     assert iwpp.iwpp_reconstruct(P(a16), P(a16), 4, 4, 8, 0, 0, P(ws + 16), 16, null) == 3

@@ -63,7 +63,7 @@ def _check(oracle_lib, cases, outs):
                                              ((16, 64), 1, 6)])
 def test_mixed_batch_static(iw, oracle_lib, tile, solver, bps):
     cases = _mixed_cases(5, 24)
-    p = iw.iwpp_default_plan()
+    p = iw.iwpp_default_batch_plan()
     p.tile_h, p.tile_w = tile
     p.local_solver = solver
     p.blocks_per_sm = bps
@@ -74,7 +74,7 @@ def test_mixed_batch_static(iw, oracle_lib, tile, solver, bps):
 @pytest.mark.parametrize("solver,bps", [(0, 0), (1, 0), (1, 6)])
 def test_uniform_batch_each_kind(iw, oracle_lib, solver, bps):
     """Batches whose images share pixel type and connectivity use the specialised kernels."""
-    p = iw.iwpp_default_plan()
+    p = iw.iwpp_default_batch_plan()
     p.tile_h, p.tile_w = (32, 32) if solver == 0 else (16, 64)
     p.local_solver = solver
     p.blocks_per_sm = bps
@@ -112,8 +112,19 @@ def test_mixed_batch_random_schedule(iw, oracle_lib):
 def test_batch_rejects_value_levels(iw):
     """Value-ordered tile queues are a single-image option: a batch call refuses the plan."""
     cases = _mixed_cases(8, 2, max_side=300)
-    p = iw.iwpp_default_plan()
+    p = iw.iwpp_default_batch_plan()
     p.value_levels = 4
+    items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
+    B = iw.Batch(items)
+    import ctypes
+    assert iw.iwpp_reconstruct_batch(B.descs, p, ctypes.c_void_p(B.ws.data_ptr()), B.ws.numel(), None) == 1
+
+
+def test_batch_rejects_coop_solver(iw):
+    """The cooperative solver (one CTA per tile) is a single-image option."""
+    cases = _mixed_cases(8, 2, max_side=300)
+    p = iw.iwpp_default_plan()
+    p.tile_h, p.tile_w, p.local_solver = 64, 64, 2
     items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
     B = iw.Batch(items)
     import ctypes
@@ -128,7 +139,7 @@ def test_batch_of_one_matches_single(iw, oracle_lib):
 
 def test_batch_small_queue_overflow(iw, oracle_lib):
     cases = _mixed_cases(7, 8, max_side=400)
-    p = iw.iwpp_default_plan()
+    p = iw.iwpp_default_batch_plan()
     p.smem_queue_cap = 16
     outs, _, _ = _run_batch(iw, cases, p)
     _check(oracle_lib, cases, outs)
@@ -201,5 +212,5 @@ def test_autotune_restores_markers_and_caches(iw, oracle_lib, tmp_path):
     assert B() == 0 and B.status() == 0
     _check(oracle_lib, cases, [m.cpu().numpy() for m, _, _, _ in items])
     # a second tuning of the same batch signature is a cache hit
-    plan2, ms2 = iw.iwpp_autotune_batch(B.descs, iw.iwpp_default_plan(), 1, cache)
+    plan2, ms2 = iw.iwpp_autotune_batch(B.descs, iw.iwpp_default_batch_plan(), 1, cache)
     assert ms2 == 0.0 and plan2.as_dict()["tile_h"] == plan.tile_h and plan2.sweeps == plan.sweeps

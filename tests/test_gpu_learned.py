@@ -122,8 +122,8 @@ def test_schedule_is_a_largest_first_permutation(iw):
     iw.iwpp_schedule_from_predictions(B.descs, None, torch.from_numpy(preds).cuda(), order, sweeps, sws)
     o = order.cpu().numpy()
     assert np.array_equal(np.sort(o), np.arange(B.ntiles))
-    # tile -> block map (the default plan's tiles inside 64 x 64 blocks), image by image
-    plan = iw.iwpp_default_plan()
+    # tile -> block map (the default batch plan's tiles inside 64 x 64 blocks), image by image
+    plan = iw.iwpp_default_batch_plan()
     th, tw = plan.tile_h, plan.tile_w
     blk = []
     bbase = 0

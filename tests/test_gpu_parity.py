@@ -73,9 +73,10 @@ def _random_pair(rng, H, W, dtype, op, vmax):
 SHAPES = [(1, 1), (1, 700), (700, 1), (32, 32), (64, 64), (65, 130), (129, 65), (200, 333), (257, 513)]
 
 
-# The two local solvers of the persistent kernel, each on a tile shape it supports.
+# The local solvers of the persistent kernel, each on a tile shape it supports.
 SOLVERS = {"queue": dict(local_solver=0, tile_h=32, tile_w=32),
-           "register": dict(local_solver=1, tile_h=16, tile_w=64)}
+           "register": dict(local_solver=1, tile_h=16, tile_w=64),
+           "coop": dict(local_solver=2, tile_h=64, tile_w=64)}
 
 
 @pytest.mark.parametrize("solver", sorted(SOLVERS))
@@ -96,12 +97,13 @@ def test_random_small(iw, oracle_lib, shape, dtype, op, conn, solver):
 EDGE_SHAPES = [(15, 63), (16, 64), (17, 65), (33, 127), (31, 128), (16, 129), (2, 2), (3, 1), (1, 3)]
 
 
-@pytest.mark.parametrize("shape", EDGE_SHAPES)
+@pytest.mark.parametrize("solver", ["register", "coop"])
+@pytest.mark.parametrize("shape", EDGE_SHAPES + [(63, 65), (64, 64), (65, 130), (129, 63)])
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 @pytest.mark.parametrize("op", ["dilate", "erode"])
-def test_register_solver_edges(iw, oracle_lib, shape, dtype, op):
+def test_register_solver_edges(iw, oracle_lib, shape, dtype, op, solver):
     rng = np.random.default_rng([102, shape[0], shape[1], op == "erode"])
-    p = _plan(iw, **SOLVERS["register"])
+    p = _plan(iw, **SOLVERS[solver])
     for conn in (4, 8):
         for vmax in (3, synth.maxval(dtype)):
             marker, mask = _random_pair(rng, *shape, dtype, op, vmax)
@@ -151,12 +153,13 @@ def test_value_ordered_queue(iw, oracle_lib, levels, bps):
     check(iw, oracle_lib, s.marker, s.mask, 8, "dilate", p)
 
 
+@pytest.mark.parametrize("solver", ["queue", "register"])
 @pytest.mark.parametrize("revisit", [0, 2])
 @pytest.mark.parametrize("bps", [0, 1])
-def test_plans_fill_holes_u16(iw, oracle_lib, revisit, bps):
+def test_plans_fill_holes_u16(iw, oracle_lib, revisit, bps, solver):
     field = synth.blob_field_u8(390, 271, 25, synth.rng_for(90))
     mask = synth.to_u16(field)
-    p = _plan(iw, revisit_sweeps=revisit, blocks_per_sm=bps, sweeps=0)
+    p = _plan(iw, revisit_sweeps=revisit, blocks_per_sm=bps, sweeps=0, **SOLVERS[solver])
     check(iw, oracle_lib, synth.fillholes_marker(mask), mask, 8, "erode", p)
 
 
@@ -165,7 +168,7 @@ def test_noise_blur_512(iw, oracle_lib):
     check(iw, oracle_lib, c.marker, c.mask, c.conn, c.op)
 
 
-@pytest.mark.parametrize("solver", [None, "queue", "register"])
+@pytest.mark.parametrize("solver", [None, "queue", "register", "coop"])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_tissue_4096(iw, oracle_lib, conn, solver):
     c = synth.tissue_case(conn=conn)
@@ -173,9 +176,20 @@ def test_tissue_4096(iw, oracle_lib, conn, solver):
     check(iw, oracle_lib, c.marker, c.mask, conn, "dilate", p)
 
 
-def test_sparse_seeds_16384(iw, oracle_lib):
+@pytest.mark.parametrize("solver", [None, "coop"])
+def test_sparse_seeds_16384(iw, oracle_lib, solver):
     c = synth.sparse_seed_case()
-    check(iw, oracle_lib, c.marker, c.mask, 8, "dilate")
+    check(iw, oracle_lib, c.marker, c.mask, 8, "dilate", _plan(iw, **SOLVERS[solver]) if solver else None)
+
+
+@pytest.mark.parametrize("bps", [0, 1, 3])
+def test_coop_fill_holes_u16(iw, oracle_lib, bps):
+    """The cooperative solver on the critical-path-bound workload: u16 fill-holes."""
+    field = synth.blob_field_u8(1000, 1300, 80, synth.rng_for(94))
+    mask = synth.to_u16(field)
+    p = _plan(iw, blocks_per_sm=bps, **SOLVERS["coop"])
+    for conn in (4, 8):
+        check(iw, oracle_lib, synth.fillholes_marker(mask), mask, conn, "erode", p)
 
 
 @pytest.mark.parametrize("conn", [8])
@@ -236,7 +250,7 @@ def test_workspace_too_small(iw):
     assert iw.iwpp_sync_status(P(ws.data_ptr()), s) == 0
 
 
-@pytest.mark.parametrize("solver", ["register", "queue"])
+@pytest.mark.parametrize("solver", ["register", "queue", "coop"])
 def test_watchdog_timeout_returns_and_workspace_recovers(iw, oracle_lib, solver):
     """A 1 ns watchdog makes an idle CTA's wait for work run out: the kernel records
     IWPP_ERR_TIMEOUT and returns (no hang, no trap); the same workspace then serves a

@@ -90,9 +90,10 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
             const bool halo = __any_sync(0xffffffffu, njt != jt || njb != jb);
             jt = njt;
             jb = njb;
-            // a strip that changed may still be short of its fixed point; one whose halo rows
+            // a strip that changed may still be short of its fixed point (its next pass pair
+            // finds out: measured cheaper than a residual check here); one whose halo rows
             // changed may have new work; the others are settled
-            active = halo || (__any_sync(0xffffffffu, ch != 0) && RT::improvable(hx, J, I, jt, jb, lane));
+            active = halo || __any_sync(0xffffffffu, ch != 0);
             if (!__syncthreads_or(active)) break;
         }
         if (w == 0 && lane == 0) st.visits++;

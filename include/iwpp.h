@@ -95,7 +95,7 @@ typedef enum {
  *                      solver does, and the strips exchange their boundary
  *                      rows through shared memory until the tile is settled
  *                      (tile_h == tile_w == 64, no sweeps, no value levels,
- *                      at most 4 CTAs per SM, single-image calls only)
+ *                      at most 4 CTAs per SM)
  *   value_levels       0 or 1: the persistent kernel's tile queue is one FIFO;
  *                      2..16: one queue per value level, and a worker takes
  *                      its next tile from the highest level that has one (the
@@ -250,7 +250,8 @@ IWPP_API int iwpp_graph_launch(iwpp_graph graph, void *stream);
 IWPP_API int iwpp_graph_destroy(iwpp_graph graph);
 
 /*
- * Autotuner: picks the local solver with its tile shape, the sweep count and
+ * Autotuner: picks the local solver with its tile shape (register 16 x 64,
+ * cooperative 64 x 64, queue 32 x 32 / 32 x 64 / 64 x 64 / 16 x 64), the sweep count and
  * (register solver) the CTAs per SM or (queue solver) the shared queue
  * capacity of *plan_inout by timing candidate
  * plans on the batch itself (coordinate descent

@@ -145,6 +145,15 @@ static size_t drain_smem(const iwpp_plan &p, const KernelSet &k) {
     return p.local_solver == IWPP_SOLVER_REGISTER ? k.reg.smem((uint32_t)p.smem_queue_cap)
                                                   : k.smem((uint32_t)p.smem_queue_cap);
 }
+// Whether the plan's solver has kernels for this set (the cooperative solver has none for
+// mixed batches, the register solver none for shapes other than 16 x 64).
+static bool has_kernels(const iwpp_plan &p, const KernelSet &k) {
+    if (p.local_solver == IWPP_SOLVER_COOP) return k.coop.scan && k.coop.drain && k.coop.smem;
+    if (p.local_solver == IWPP_SOLVER_REGISTER)
+        return k.reg.scan && k.reg.smem && (p.blocks_per_sm > kRegBlocks ? k.reg.drain_hi : k.reg.drain);
+    return k.scan && k.drain && k.smem;
+}
+
 // Tiles one persistent CTA works on at a time: one per warp, or one per CTA (cooperative).
 static int tiles_per_cta(const iwpp_plan &p) { return p.local_solver == IWPP_SOLVER_COOP ? 1 : kWarpsPerCta; }
 
@@ -152,7 +161,9 @@ static int tiles_per_cta(const iwpp_plan &p) { return p.local_solver == IWPP_SOL
 // CTAs than needed to give every tile its own warp.
 static int drain_grid(const iwpp_plan &p, int v, uint32_t ntiles) {
     const int shape = shape_index(p.tile_h, p.tile_w);
+    if (shape < 0) return 0;
     const KernelSet &k = kernels(shape, v);
+    if (!has_kernels(p, k)) return 0;
     const size_t smem = drain_smem(p, k);
     if (ensure_smem_attr(shape, v, k.smem((uint32_t)p.smem_queue_cap)) != cudaSuccess) return 0;
     int bps = p.blocks_per_sm;
@@ -413,8 +424,7 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
                       cudaStream_t stream) {
     iwpp_plan p;
     if (plan_in) p = *plan_in; else default_batch_plan(&p);
-    if (!plan_valid(p) || p.value_levels > 1 || p.local_solver == IWPP_SOLVER_COOP)
-        return IWPP_ERR_ARG;   // batches: one FIFO, one tile per warp
+    if (!plan_valid(p) || p.value_levels > 1) return IWPP_ERR_ARG;   // batches: one FIFO
     if (!imgs || n < 1) return IWPP_ERR_ARG;
     for (int i = 0; i < n; i++)
         if (check_image(imgs[i]) != IWPP_OK) return IWPP_ERR_ARG;

@@ -6,7 +6,8 @@
 // that crosses the tile vertically then costs a few passes instead of several trips through
 // the tile queue, which is what bounds the drain when one chain of tile hops is the critical
 // path. The tile queue protocol (pop, notify, finish) is the persistent engine's, run by warp 0
-// on behalf of the CTA.
+// on behalf of the CTA. Kernels specialised on pixel type and connectivity serve single
+// images and uniform batches; the mixed build dispatches on each tile's image kind.
 #pragma once
 
 #include "iwpp_regtile.cuh"
@@ -125,7 +126,26 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
     st.waves += passes;
 }
 
-template <typename T, int CONN>
+// One CTA tile visit, dispatched on the tile's image kind (CTA-uniform: one tile per CTA).
+template <typename T, int CONN, bool MIXED>
+__device__ __forceinline__ void visit_tile_coop_any(const EngineArgs &a, uint32_t t, uint8_t *wsmem, CoopShared &C,
+                                                    VisitStats &st, int w, int lane) {
+    const ImageView &im = image_of(a, t);
+    if (!MIXED) {
+        visit_tile_coop<T, CONN>(a, im, t, wsmem, C, st, w, lane);
+        return;
+    }
+    switch (im.kind) {
+        case 0: visit_tile_coop<uint8_t, 4>(a, im, t, wsmem, C, st, w, lane); break;
+        case 1: visit_tile_coop<uint16_t, 4>(a, im, t, wsmem, C, st, w, lane); break;
+        case 2: visit_tile_coop<uint8_t, 8>(a, im, t, wsmem, C, st, w, lane); break;
+        default: visit_tile_coop<uint16_t, 8>(a, im, t, wsmem, C, st, w, lane); break;
+    }
+}
+
+// The persistent kernel: warp 0 pops a tile for the CTA, the CTA visits it. MIXED: a batch
+// whose images differ in pixel type or connectivity (T, CONN unused).
+template <typename T, int CONN, bool MIXED>
 __global__ void __launch_bounds__(kThreads, kRegBlocks) drain_coop_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -144,41 +164,60 @@ __global__ void __launch_bounds__(kThreads, kRegBlocks) drain_coop_kernel(Engine
         const uint32_t t = C.tile;
         if (t == kDone) break;
         const unsigned long long b0 = globaltimer_ns();
-        visit_tile_coop<T, CONN>(a, a.img0, t, wsmem, C, st, warp, lane);
+        visit_tile_coop_any<T, CONN, MIXED>(a, t, wsmem, C, st, warp, lane);
         if (warp == 0) busy += globaltimer_ns() - b0;
         __syncthreads();   // every warp has read C.tile before the next pop overwrites it
     }
     flush_stats(a, st, idle, busy, lane);
 }
 
-// Initial frontier: queue every CTA tile one of whose pixels can rise (each strip checks its
-// own pixels against its neighbourhood, halo included), and check the precondition.
+// Initial frontier of one CTA tile: queue it if one of its pixels can rise (each strip checks
+// its own pixels against its neighbourhood, halo included), and check the precondition.
 template <typename T, int CONN>
-__global__ void __launch_bounds__(kThreads) scan_coop_kernel(EngineArgs a) {
+__device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem, int w,
+                               int lane) {
     constexpr int TH = kCoopStrip;
     using RT = RegTile<T, CONN, TH>;
+    const typename RT::Smem s = RT::carve(wsmem);
+    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const uint32_t lt = t - im.tile_base;
+    const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
+    const int y0 = ty * kCoopRows + TH * w, x0 = tx * RT::TW;
+    uint32_t J[TH], I[TH], jt, jb, it, ib;
+    RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
+    const bool can = RT::improvable(hx, J, I, jt, jb, lane);
+    const int any_bad = __syncthreads_or(bad);
+    const int any_can = __syncthreads_or(can);
+    if (threadIdx.x == 0) {
+        if (any_can) {
+            if (a.defer_push) mark_pending(a, t); else notify_tile(a, t);   // batches: queued in order later
+        }
+        if (any_bad) set_status(a.hdr, kErrPrecondition);
+    }
+    __syncthreads();   // the strips' shared halo buffers are reloaded for the next tile
+}
+
+template <typename T, int CONN, bool MIXED>
+__global__ void __launch_bounds__(kThreads) scan_coop_kernel(EngineArgs a) {
+    using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const typename RT::Smem s = RT::carve(smem_raw + w * RT::smem_per_warp(0));
-    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
-    const ImageView &im = a.img0;
+    uint8_t *wsmem = smem_raw + w * RT::smem_per_warp(0);
     for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const uint32_t lt = t - im.tile_base;
-        const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
-        const int y0 = ty * kCoopRows + TH * w, x0 = tx * RT::TW;
-        uint32_t J[TH], I[TH], jt, jb, it, ib;
-        RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
-        bool bad = false;
-#pragma unroll
-        for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
-        const bool can = RT::improvable(hx, J, I, jt, jb, lane);
-        const int any_bad = __syncthreads_or(bad);
-        const int any_can = __syncthreads_or(can);
-        if (threadIdx.x == 0) {
-            if (any_can) notify_tile(a, t);
-            if (any_bad) set_status(a.hdr, kErrPrecondition);
+        const ImageView &im = image_of(a, t);
+        if (!MIXED) {
+            scan_tile_coop<T, CONN>(a, im, t, wsmem, w, lane);
+            continue;
         }
-        __syncthreads();   // the strips' shared halo buffers are reloaded for the next tile
+        switch (im.kind) {
+            case 0: scan_tile_coop<uint8_t, 4>(a, im, t, wsmem, w, lane); break;
+            case 1: scan_tile_coop<uint16_t, 4>(a, im, t, wsmem, w, lane); break;
+            case 2: scan_tile_coop<uint8_t, 8>(a, im, t, wsmem, w, lane); break;
+            default: scan_tile_coop<uint16_t, 8>(a, im, t, wsmem, w, lane); break;
+        }
     }
 }
 

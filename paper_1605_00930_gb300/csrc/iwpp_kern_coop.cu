@@ -5,11 +5,11 @@
 
 namespace iwpp {
 
-template <typename T, int CONN>
+template <typename T, int CONN, bool MIXED = false>
 static RegKernelSet coop_set() {
     RegKernelSet k;
-    k.scan = scan_coop_kernel<T, CONN>;
-    k.drain = drain_coop_kernel<T, CONN>;
+    k.scan = scan_coop_kernel<T, CONN, MIXED>;
+    k.drain = drain_coop_kernel<T, CONN, MIXED>;
     k.drain_hi = nullptr;   // one build: 4 CTAs of 4 warps per SM
     k.smem = &coop_smem_fn<T, CONN>;
     return k;
@@ -23,7 +23,8 @@ RegKernelSet coop_kernel_set(int th, int tw, int v) {
         case 1: return coop_set<uint16_t, 4>();
         case 2: return coop_set<uint8_t, 8>();
         case 3: return coop_set<uint16_t, 8>();
-        default: return none;   // single-image kinds only
+        case 4: return coop_set<uint16_t, 8, true>();   // mixed batches
+        default: return none;
     }
 }
 

@@ -189,7 +189,7 @@ static void cache_store(const char *path, const std::string &key, const iwpp_pla
 int autotune(const iwpp_image *imgs, int n, iwpp_plan *plan, int reps, const char *cache_path,
              cudaStream_t stream, float *best_ms) {
     if (!imgs || n < 1 || !plan) return IWPP_ERR_ARG;
-    if (!plan_valid(*plan) || plan->local_solver == IWPP_SOLVER_COOP) return IWPP_ERR_ARG;   // batches only
+    if (!plan_valid(*plan)) return IWPP_ERR_ARG;
     for (int i = 0; i < n; i++)
         if (batch_tiles(imgs + i, 1, *plan, nullptr) < 1) return IWPP_ERR_ARG;
     const std::string key = cache_key(imgs, n);
@@ -215,9 +215,9 @@ int autotune(const iwpp_image *imgs, int n, iwpp_plan *plan, int reps, const cha
         }
     };
     // {tile_h, tile_w, local_solver}
-    static const int shapes[5][3] = {{16, 64, IWPP_SOLVER_REGISTER}, {32, 32, IWPP_SOLVER_QUEUE},
-                                     {32, 64, IWPP_SOLVER_QUEUE}, {64, 64, IWPP_SOLVER_QUEUE},
-                                     {16, 64, IWPP_SOLVER_QUEUE}};
+    static const int shapes[6][3] = {{16, 64, IWPP_SOLVER_REGISTER}, {64, 64, IWPP_SOLVER_COOP},
+                                     {32, 32, IWPP_SOLVER_QUEUE},    {32, 64, IWPP_SOLVER_QUEUE},
+                                     {64, 64, IWPP_SOLVER_QUEUE},    {16, 64, IWPP_SOLVER_QUEUE}};
     iwpp_plan base = best;
     for (const auto &sh : shapes) {
         iwpp_plan c = base;

@@ -60,7 +60,7 @@ def _check(oracle_lib, cases, outs):
 
 @pytest.mark.parametrize("tile,solver,bps", [((32, 32), 0, 0), ((32, 64), 0, 0), ((64, 64), 0, 0),
                                              ((16, 32), 0, 0), ((16, 64), 0, 0), ((16, 64), 1, 0),
-                                             ((16, 64), 1, 6)])
+                                             ((16, 64), 1, 6), ((64, 64), 2, 0), ((64, 64), 2, 3)])
 def test_mixed_batch_static(iw, oracle_lib, tile, solver, bps):
     cases = _mixed_cases(5, 24)
     p = iw.iwpp_default_batch_plan()
@@ -71,11 +71,12 @@ def test_mixed_batch_static(iw, oracle_lib, tile, solver, bps):
     _check(oracle_lib, cases, outs)
 
 
-@pytest.mark.parametrize("solver,bps", [(0, 0), (1, 0), (1, 6)])
+@pytest.mark.parametrize("solver,bps", [(0, 0), (1, 0), (1, 6), (2, 0), (2, 2)])
 def test_uniform_batch_each_kind(iw, oracle_lib, solver, bps):
-    """Batches whose images share pixel type and connectivity use the specialised kernels."""
+    """Batches whose images share pixel type and connectivity use the specialised kernels
+    (the cooperative solver among them)."""
     p = iw.iwpp_default_batch_plan()
-    p.tile_h, p.tile_w = (32, 32) if solver == 0 else (16, 64)
+    p.tile_h, p.tile_w = {0: (32, 32), 1: (16, 64), 2: (64, 64)}[solver]
     p.local_solver = solver
     p.blocks_per_sm = bps
     for k, (dtype, conn) in enumerate([(np.uint8, 4), (np.uint16, 4), (np.uint8, 8), (np.uint16, 8)]):
@@ -109,22 +110,29 @@ def test_mixed_batch_random_schedule(iw, oracle_lib):
     assert work[B.ntiles:].sum() > 0   # cycles recorded for the tiles
 
 
+def test_coop_batch_with_schedule(iw, oracle_lib):
+    """A uniform batch under the cooperative solver with an explicit tile order (repeated and
+    missing ids) and per-tile sweep counts (which the cooperative solver does not run)."""
+    cases = [synth.sparse_seed_case(700, 1100, nblobs=30, nseeds=6, image_idx=i) for i in range(3)]
+    p = iw.iwpp_default_batch_plan()
+    p.tile_h, p.tile_w, p.local_solver = 64, 64, 2
+
+    def schedule(nt):
+        g = torch.Generator().manual_seed(5)
+        order = torch.randperm(nt, generator=g).to(torch.int32)
+        order[: nt // 8] = order[nt // 8: 2 * (nt // 8)]
+        sweeps = torch.randint(0, 5, (nt,), generator=g, dtype=torch.uint8)
+        return {"order": order.cuda(), "sweeps": sweeps.cuda()}
+
+    outs, _, _ = _run_batch(iw, cases, p, schedule)
+    _check(oracle_lib, cases, outs)
+
+
 def test_batch_rejects_value_levels(iw):
     """Value-ordered tile queues are a single-image option: a batch call refuses the plan."""
     cases = _mixed_cases(8, 2, max_side=300)
     p = iw.iwpp_default_batch_plan()
     p.value_levels = 4
-    items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
-    B = iw.Batch(items)
-    import ctypes
-    assert iw.iwpp_reconstruct_batch(B.descs, p, ctypes.c_void_p(B.ws.data_ptr()), B.ws.numel(), None) == 1
-
-
-def test_batch_rejects_coop_solver(iw):
-    """The cooperative solver (one CTA per tile) is a single-image option."""
-    cases = _mixed_cases(8, 2, max_side=300)
-    p = iw.iwpp_default_plan()
-    p.tile_h, p.tile_w, p.local_solver = 64, 64, 2
     items = [(torch.from_numpy(c.marker).cuda(), torch.from_numpy(c.mask).cuda(), c.conn, c.op) for c in cases]
     B = iw.Batch(items)
     import ctypes

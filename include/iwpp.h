@@ -95,7 +95,7 @@ typedef enum {
  *                      solver does, and the strips exchange their boundary
  *                      rows through shared memory until the tile is settled
  *                      (tile_h == tile_w == 64, no sweeps, no value levels,
- *                      at most 4 CTAs per SM)
+ *                      at most 5 CTAs per SM)
  *   value_levels       0 or 1: the persistent kernel's tile queue is one FIFO;
  *                      2..16: one queue per value level, and a worker takes
  *                      its next tile from the highest level that has one (the

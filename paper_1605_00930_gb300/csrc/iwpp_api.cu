@@ -190,7 +190,7 @@ bool plan_valid(const iwpp_plan &p) {
         p.local_solver != IWPP_SOLVER_COOP)
         return false;
     if (p.local_solver == IWPP_SOLVER_COOP &&
-        (!coop_kernel_set(p.tile_h, p.tile_w, 0).drain || p.value_levels > 1 || p.blocks_per_sm > kRegBlocks ||
+        (!coop_kernel_set(p.tile_h, p.tile_w, 0).drain || p.value_levels > 1 || p.blocks_per_sm > kCoopBlocks ||
          p.sweeps != 0 || p.revisit_sweeps != 0))
         return false;
     if (p.local_solver == IWPP_SOLVER_REGISTER && !reg_kernel_set(p.tile_h, p.tile_w, 0).drain) return false;

@@ -22,6 +22,7 @@ struct RegKernelSet {
     size_t (*smem)(uint32_t);
 };
 constexpr int kRegBlocks = 4, kRegHiBlocks = 6;
+constexpr int kCoopBlocks = 5;   // CTAs per SM of the cooperative solver's persistent kernel
 RegKernelSet reg_kernel_set(int th, int tw, int v);
 RegKernelSet coop_kernel_set(int th, int tw, int v);   // cooperative solver (64 x 64 tiles)
 

@@ -9,9 +9,11 @@
 // smallest labels, max of the largest). That update is a join on a distributive lattice, so
 // every order of work reaches the same fixed point: d = the geodesic distance to the
 // nearest marker and the labels of all markers at that distance. Pixels outside the domain
-// carry d = kBlocked and never change. A visit holds a 16 x 64 tile in registers (lane c:
-// columns 2c and 2c + 1) and repeats down / up passes until a pass pair changes nothing; a
-// halo pixel that the tile's border would change marks its tile for a visit.
+// carry d = kBlocked and never change. One CTA settles a 64 x 64 tile: each of its four warps
+// holds a 16-row strip in registers (lane c: columns 2c and 2c + 1) and repeats down / up
+// passes; the strips exchange their first and last rows through shared memory between pass
+// pairs until none changes (the reconstruction's cooperative tile); a halo pixel that the
+// tile's border would change marks its tile for a visit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -27,6 +29,8 @@ constexpr uint32_t kUnr = 0xC0000000u;      // domain pixel not reached yet (rea
 constexpr uint32_t kBlocked = 0xE0000000u;  // outside the domain (also outside the image)
 constexpr uint32_t kNoLab = 0xFFFFFFFFu;
 constexpr int STH = 16, STW = 64;
+constexpr int SKW = kWarpsPerCta;   // strips per CTA tile
+constexpr int SCH = STH * SKW;      // CTA tile rows
 
 struct St {
     uint32_t d, l;
@@ -246,57 +250,133 @@ __device__ void sk_store(const ImageView &im, int y0, int x0, const SkTile &T, u
     }
 }
 
+// The CTA tile's shared state: each strip's first and last row (d and l of the even and
+// odd pixel per lane), the tile's notification flags, the popped tile.
+struct SkShared {
+    uint32_t rows[SKW][8][32];
+    uint32_t misc[16];
+    uint32_t tile, redo;
+};
+constexpr size_t kSkSmemCta = kSkSmemPerWarp * SKW + sizeof(SkShared);
+
+// Fold one strip's notification flags into the CTA tile's (as for the reconstruction's
+// cooperative tile: a strip's top / bottom side is the tile's only for the first / last
+// strip, and its corners beside the tile's inner rows lie in the west / east neighbours).
+__device__ __forceinline__ void sk_fold_misc(SkShared &C, const uint32_t *m, int w) {
+    if (w == 0) {
+        atomicOr(&C.misc[0], m[0]);
+        atomicOr(&C.misc[1], m[1]);
+        atomicOr(&C.misc[2], m[2]);
+    } else {
+        atomicOr(&C.misc[3], m[0]);
+        atomicOr(&C.misc[5], m[2]);
+    }
+    if (w == SKW - 1) {
+        atomicOr(&C.misc[6], m[6]);
+        atomicOr(&C.misc[7], m[7]);
+        atomicOr(&C.misc[8], m[8]);
+    } else {
+        atomicOr(&C.misc[3], m[6]);
+        atomicOr(&C.misc[5], m[8]);
+    }
+    atomicOr(&C.misc[3], m[3]);
+    atomicOr(&C.misc[5], m[5]);
+}
+
+// One visit of CTA tile t by the whole CTA (every thread calls it with the same t), including
+// the re-processing rounds when the tile is notified while the CTA holds it.
 template <int CONN>
-__device__ void sk_visit(const EngineArgs &a, uint32_t t, uint8_t *wsmem, VisitStats &st, int lane) {
+__device__ void sk_visit(const EngineArgs &a, uint32_t t, uint8_t *wsmem, SkShared &C, VisitStats &st, int w,
+                         int lane) {
     const ImageView &im = a.img0;
     const SkSmem s = sk_carve(wsmem);
     const int ty = (int)(t / im.tiles_x), tx = (int)(t % im.tiles_x);
-    const int y0 = ty * STH, x0 = tx * STW;
+    const int y0 = ty * SCH + STH * w, x0 = tx * STW;
     if (lane < 16) s.misc[lane] = 0;
+    if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
     SkTile T;
     sk_load(im, s, y0, x0, T, lane);
     uint32_t passes = 0;
     for (;;) {
         uint32_t rows = 0;
-        for (;;) {
-            uint32_t ch = sk_pass<CONN, 1>(s, T, lane);
-            ch |= sk_pass<CONN, -1>(s, T, lane);
-            passes += 2;
-            rows |= ch;
-            if (!__any_sync(0xffffffffu, ch != 0)) break;
+        bool active = true;
+        for (;;) {   // joint iterations of the strips
+            uint32_t ch = 0;
+            if (active) {
+                ch = sk_pass<CONN, 1>(s, T, lane);
+                ch |= sk_pass<CONN, -1>(s, T, lane);
+                passes += 2;
+                rows |= ch;
+            }
+            C.rows[w][0][lane] = T.e[0].d;
+            C.rows[w][1][lane] = T.e[0].l;
+            C.rows[w][2][lane] = T.o[0].d;
+            C.rows[w][3][lane] = T.o[0].l;
+            C.rows[w][4][lane] = T.e[STH - 1].d;
+            C.rows[w][5][lane] = T.e[STH - 1].l;
+            C.rows[w][6][lane] = T.o[STH - 1].d;
+            C.rows[w][7][lane] = T.o[STH - 1].l;
+            __syncthreads();
+            St nte = T.te, nto = T.to, nbe = T.be, nbo = T.bo;
+            if (w > 0) {
+                nte = St{C.rows[w - 1][4][lane], C.rows[w - 1][5][lane]};
+                nto = St{C.rows[w - 1][6][lane], C.rows[w - 1][7][lane]};
+            }
+            if (w < SKW - 1) {
+                nbe = St{C.rows[w + 1][0][lane], C.rows[w + 1][1][lane]};
+                nbo = St{C.rows[w + 1][2][lane], C.rows[w + 1][3][lane]};
+            }
+            const bool halo =
+                __any_sync(0xffffffffu, neq(nte, T.te) || neq(nto, T.to) || neq(nbe, T.be) || neq(nbo, T.bo));
+            T.te = nte;
+            T.to = nto;
+            T.be = nbe;
+            T.bo = nbo;
+            const bool active_next = halo || __any_sync(0xffffffffu, ch != 0);
+            active = active_next;
+            if (!__syncthreads_or(active)) break;
         }
-        st.visits++;
-        const bool changed = __any_sync(0xffffffffu, rows != 0);
-        if (changed) {
+        if (w == 0 && lane == 0) st.visits++;
+        if (__syncthreads_or(rows != 0)) {
             sk_store(im, y0, x0, T, rows, lane);
             sk_notify_scan<CONN>(s, T, lane);
+            if (lane == 0) sk_fold_misc(C, s.misc, w);
             __threadfence();
-            __syncwarp();
+            __syncthreads();
+            if (w == 0 && lane < 9 && lane != 4 && C.misc[lane]) {
+                const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+                if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
+                    notify_tile(a, (uint32_t)(ny * im.tiles_x + nx));
+            }
         }
-        if (changed && lane < 9 && lane != 4 && s.misc[lane]) {
-            const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
-            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
-                notify_tile(a, (uint32_t)(ny * im.tiles_x + nx));
+        if (w == 0) {
+            const bool r = finish_tile(a, t, lane);
+            if (lane == 0) C.redo = r;
         }
-        if (!finish_tile(a, t, lane)) break;
-        __syncwarp();
+        __syncthreads();
+        const bool redo = C.redo != 0;
+        if (!redo) break;
+        // re-process: the strips stay in registers; only the tile's halo can have changed
         if (lane < 16) s.misc[lane] = 0;
+        if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
         sk_load_halo(im, s, y0, x0, T, lane);
+        __syncthreads();
     }
     st.waves += passes;
 }
 
-// Initialisation: markers take (0, their label), other domain pixels are unreached, the rest
-// blocked; every tile holding a marker is queued. Labels above 65534 stop the call with
-// IWPP_ERR_ARG.
-__global__ void __launch_bounds__(256) sk_init_kernel(EngineArgs a, const uint32_t *markers, const uint8_t *mask) {
+// Initialisation, one warp per 16 x 64 strip: markers take (0, their label), other domain
+// pixels are unreached, the rest blocked; the CTA tile of every strip holding a marker is
+// queued. Labels above 65534 stop the call with IWPP_ERR_ARG.
+__global__ void __launch_bounds__(256) sk_init_kernel(EngineArgs a, const uint32_t *markers, const uint8_t *mask,
+                                                      uint32_t nstrips) {
     const ImageView &im = a.img0;
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long *V = reinterpret_cast<unsigned long long *>(im.J);
-    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.ntiles; t += nw) {
-        const int ty = (int)(t / im.tiles_x), tx = (int)(t % im.tiles_x);
-        const int y0 = ty * STH, x0 = tx * STW;
+    for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nstrips; u += nw) {
+        const int uy = (int)(u / im.tiles_x), ux = (int)(u % im.tiles_x);
+        const int y0 = uy * STH, x0 = ux * STW;
         bool any = false, bad = false;
         for (int r = 0; r < STH; r++) {
             const int y = y0 + r;
@@ -319,7 +399,7 @@ __global__ void __launch_bounds__(256) sk_init_kernel(EngineArgs a, const uint32
         bad = __any_sync(0xffffffffu, bad);
         __threadfence();
         if (lane == 0 && bad) set_status(a.hdr, kErrArg);
-        if (lane == 0 && any) notify_tile(a, t);
+        if (lane == 0 && any) notify_tile(a, (uint32_t)((uy / SKW) * im.tiles_x + ux));
     }
 }
 
@@ -328,15 +408,22 @@ __global__ void __launch_bounds__(kThreads, 2) sk_drain_kernel(EngineArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *wsmem = smem_raw + warp * kSkSmemPerWarp;
+    SkShared &C = *reinterpret_cast<SkShared *>(smem_raw + SKW * kSkSmemPerWarp);
     VisitStats st = {0, 0, 0, 0};
     unsigned long long idle = 0, busy = 0;
     for (;;) {
-        bool first;
-        const uint32_t t = acquire_tile(a, first, idle, lane);
+        if (warp == 0) {
+            bool first;
+            const uint32_t t = acquire_tile(a, first, idle, lane);
+            if (lane == 0) C.tile = t;
+        }
+        __syncthreads();
+        const uint32_t t = C.tile;
         if (t == kDone) break;
         const unsigned long long b0 = globaltimer_ns();
-        sk_visit<CONN>(a, t, wsmem, st, lane);
-        busy += globaltimer_ns() - b0;
+        sk_visit<CONN>(a, t, wsmem, C, st, warp, lane);
+        if (warp == 0) busy += globaltimer_ns() - b0;
+        __syncthreads();   // every warp has read C.tile before the next pop overwrites it
     }
     flush_stats(a, st, idle, busy, lane);
 }
@@ -357,17 +444,18 @@ __global__ void sk_finish_kernel(const unsigned long long *V, uint32_t *zone, in
 
 struct SkLayout {
     size_t state, queue, px, total;
-    uint32_t ntiles;
+    uint32_t ntiles, nstrips;   // 64 x 64 CTA tiles; 16 x 64 strips
     int tiles_x, tiles_y;
 };
 
 bool sk_layout(int64_t H, int64_t W, SkLayout &L) {
     if (H < 1 || W < 1 || H >= (1ll << 31) || W >= (1ll << 31) || (uint64_t)H * (uint64_t)W >= (1ull << 31))
         return false;
-    const uint64_t tx = (uint64_t)((W + STW - 1) / STW), ty = (uint64_t)((H + STH - 1) / STH);
+    const uint64_t tx = (uint64_t)((W + STW - 1) / STW), ty = (uint64_t)((H + SCH - 1) / SCH);
     L.tiles_x = (int)tx;
     L.tiles_y = (int)ty;
     L.ntiles = (uint32_t)(tx * ty);
+    L.nstrips = (uint32_t)(tx * (uint64_t)((H + STH - 1) / STH));
     L.state = 256;
     L.queue = L.state + align256((size_t)L.ntiles * 4);
     L.px = L.queue + align256((size_t)L.ntiles * 4);
@@ -415,17 +503,16 @@ extern "C" int iwpp_skiz(const uint32_t *markers, const uint8_t *mask, uint32_t 
     if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4, s) != cudaSuccess) return IWPP_ERR_CUDA;
     const int sms = device_sm_count();
     if (sms <= 0) return IWPP_ERR_CUDA;
-    uint32_t ig = (L.ntiles + 7) / 8;
+    uint32_t ig = (L.nstrips + 7) / 8;
     if (ig > (uint32_t)sms * 8) ig = (uint32_t)sms * 8;
-    sk_init_kernel<<<ig, 256, 0, s>>>(a, markers, mask);
-    const size_t smem = kSkSmemPerWarp * kWarpsPerCta;
+    sk_init_kernel<<<ig, 256, 0, s>>>(a, markers, mask, L.nstrips);
+    const size_t smem = kSkSmemCta;
     void (*drain)(EngineArgs) = connectivity == 8 ? sk_drain_kernel<8> : sk_drain_kernel<4>;
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, drain, kThreads, smem) != cudaSuccess || bps < 1)
         return IWPP_ERR_CUDA;
     long long g = (long long)bps * sms;
-    const long long need = ((long long)L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
-    if (g > need) g = need;
+    if (g > (long long)L.ntiles) g = L.ntiles;   // one CTA per tile
     drain<<<(int)g, kThreads, smem, s>>>(a);
     const size_t n = (size_t)H * (size_t)W;
     sk_finish_kernel<<<sms * 8, 256, 0, s>>>(reinterpret_cast<const unsigned long long *>(base + L.px), zone_out,

@@ -4,10 +4,11 @@
 // Every pixel carries a pair packed as (level << 16) | label, 0xFFFFFFFF while unreached.
 // Markers are fixed at (gradient, label). A neighbour q offers pixel p the pair
 // (max(level(q), gradient(p)), label(q)) — in the packing, max(v_q, gradient(p) << 16 |
-// label(q)) — and p keeps the smaller of its own pair and every offer. A visit holds a
-// 16 x 64 tile in registers (lane c: columns 2c and 2c + 1; the gradient packed as u16x2)
-// and repeats down / up passes of that update until a pass pair changes nothing; a halo
-// pixel that the tile's border would improve marks its tile for a visit. The levels reached
+// label(q)) — and p keeps the smaller of its own pair and every offer. One CTA settles a
+// 64 x 64 tile: each of its four warps holds a 16-row strip in registers (lane c: columns 2c
+// and 2c + 1; the gradient packed as u16x2) and repeats down / up passes of that update; the
+// strips exchange their first and last rows through shared memory between pass pairs until
+// none changes; a halo pixel that the tile's border would improve marks its tile for a visit. The levels reached
 // are unique (the minimax flooding level); which label wins where several reach a pixel at
 // its level depends on the order of work, as in any flooding watershed.
 #include <cuda_runtime.h>
@@ -23,6 +24,8 @@ namespace {
 
 constexpr uint32_t kUnreached = 0xFFFFFFFFu;
 constexpr int WTH = 16, WTW = 64;
+constexpr int WSW = kWarpsPerCta;   // strips per CTA tile
+constexpr int WCH = WTH * WSW;      // CTA tile rows
 
 // The offer of pair v (at a neighbour) to a pixel whose gradient is g (already << 16).
 __device__ __forceinline__ uint32_t offer_ws(uint32_t v, uint32_t g16) { return max(v, g16 | (v & 0xFFFFu)); }
@@ -233,57 +236,126 @@ __device__ void ws_store(const ImageView &im, int y0, int x0, const WsTile &T, u
     }
 }
 
+// The CTA tile's shared state: each strip's first and last row (even and odd pair per lane),
+// the tile's notification flags, the popped tile.
+struct WsShared {
+    uint32_t rows[WSW][4][32];
+    uint32_t misc[16];
+    uint32_t tile, redo;
+};
+constexpr size_t kWsSmemCta = kWsSmemPerWarp * WSW + sizeof(WsShared);
+
+// Fold one strip's notification flags into the CTA tile's (a strip's top / bottom side is the
+// tile's only for the first / last strip; its corners beside the tile's inner rows lie in the
+// west / east neighbours).
+__device__ __forceinline__ void ws_fold_misc(WsShared &C, const uint32_t *m, int w) {
+    if (w == 0) {
+        atomicOr(&C.misc[0], m[0]);
+        atomicOr(&C.misc[1], m[1]);
+        atomicOr(&C.misc[2], m[2]);
+    } else {
+        atomicOr(&C.misc[3], m[0]);
+        atomicOr(&C.misc[5], m[2]);
+    }
+    if (w == WSW - 1) {
+        atomicOr(&C.misc[6], m[6]);
+        atomicOr(&C.misc[7], m[7]);
+        atomicOr(&C.misc[8], m[8]);
+    } else {
+        atomicOr(&C.misc[3], m[6]);
+        atomicOr(&C.misc[5], m[8]);
+    }
+    atomicOr(&C.misc[3], m[3]);
+    atomicOr(&C.misc[5], m[5]);
+}
+
+// One visit of CTA tile t by the whole CTA (every thread calls it with the same t), including
+// the re-processing rounds when the tile is notified while the CTA holds it.
 template <int CONN>
-__device__ void ws_visit(const EngineArgs &a, const WsArgs &w, uint32_t t, uint8_t *wsmem, VisitStats &st,
-                         int lane) {
+__device__ void ws_visit(const EngineArgs &a, const WsArgs &wa, uint32_t t, uint8_t *wsmem, WsShared &C,
+                         VisitStats &st, int w, int lane) {
     const ImageView &im = a.img0;
     const WsSmem s = ws_carve(wsmem);
     const int ty = (int)(t / im.tiles_x), tx = (int)(t % im.tiles_x);
-    const int y0 = ty * WTH, x0 = tx * WTW;
+    const int y0 = ty * WCH + WTH * w, x0 = tx * WTW;
     if (lane < 16) s.misc[lane] = 0;
+    if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
     WsTile T;
-    ws_load(im, w, s, y0, x0, T, lane);
+    ws_load(im, wa, s, y0, x0, T, lane);
     uint32_t passes = 0;
     for (;;) {
         uint32_t rows = 0;
-        for (;;) {
-            uint32_t ch = ws_pass<CONN, 1>(s, T, lane);
-            ch |= ws_pass<CONN, -1>(s, T, lane);
-            passes += 2;
-            rows |= ch;
-            if (!__any_sync(0xffffffffu, ch != 0)) break;
+        bool active = true;
+        for (;;) {   // joint iterations of the strips
+            uint32_t ch = 0;
+            if (active) {
+                ch = ws_pass<CONN, 1>(s, T, lane);
+                ch |= ws_pass<CONN, -1>(s, T, lane);
+                passes += 2;
+                rows |= ch;
+            }
+            C.rows[w][0][lane] = T.e[0];
+            C.rows[w][1][lane] = T.o[0];
+            C.rows[w][2][lane] = T.e[WTH - 1];
+            C.rows[w][3][lane] = T.o[WTH - 1];
+            __syncthreads();
+            uint32_t nte = T.te, nto = T.to, nbe = T.be, nbo = T.bo;
+            if (w > 0) {
+                nte = C.rows[w - 1][2][lane];
+                nto = C.rows[w - 1][3][lane];
+            }
+            if (w < WSW - 1) {
+                nbe = C.rows[w + 1][0][lane];
+                nbo = C.rows[w + 1][1][lane];
+            }
+            const bool halo = __any_sync(0xffffffffu, nte != T.te || nto != T.to || nbe != T.be || nbo != T.bo);
+            T.te = nte;
+            T.to = nto;
+            T.be = nbe;
+            T.bo = nbo;
+            active = halo || __any_sync(0xffffffffu, ch != 0);
+            if (!__syncthreads_or(active)) break;
         }
-        st.visits++;
-        const bool changed = __any_sync(0xffffffffu, rows != 0);
-        if (changed) {
+        if (w == 0 && lane == 0) st.visits++;
+        if (__syncthreads_or(rows != 0)) {
             ws_store(im, y0, x0, T, rows, lane);
             ws_notify_scan<CONN>(s, T, lane);
+            if (lane == 0) ws_fold_misc(C, s.misc, w);
             __threadfence();
-            __syncwarp();
+            __syncthreads();
+            if (w == 0 && lane < 9 && lane != 4 && C.misc[lane]) {
+                const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+                if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
+                    notify_tile(a, (uint32_t)(ny * im.tiles_x + nx));
+            }
         }
-        if (changed && lane < 9 && lane != 4 && s.misc[lane]) {
-            const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
-            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
-                notify_tile(a, (uint32_t)(ny * im.tiles_x + nx));
+        if (w == 0) {
+            const bool r = finish_tile(a, t, lane);
+            if (lane == 0) C.redo = r;
         }
-        if (!finish_tile(a, t, lane)) break;
-        __syncwarp();
+        __syncthreads();
+        const bool redo = C.redo != 0;
+        if (!redo) break;
+        // re-process: the strips stay in registers; only the tile's halo can have changed
         if (lane < 16) s.misc[lane] = 0;
-        ws_load_halo(im, w, s, y0, x0, T, false, lane);
+        if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
+        ws_load_halo(im, wa, s, y0, x0, T, false, lane);
+        __syncthreads();
     }
     st.waves += passes;
 }
 
-// Initialisation: markers take (gradient, label), everything else is unreached; every tile
-// holding a marker is queued. Labels above 65534 stop the call with IWPP_ERR_ARG.
-__global__ void __launch_bounds__(256) ws_init_kernel(EngineArgs a, WsArgs w) {
+// Initialisation, one warp per 16 x 64 strip: markers take (gradient, label), everything else
+// is unreached; the CTA tile of every strip holding a marker is queued. Labels above 65534
+// stop the call with IWPP_ERR_ARG.
+__global__ void __launch_bounds__(256) ws_init_kernel(EngineArgs a, WsArgs w, uint32_t nstrips) {
     const ImageView &im = a.img0;
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     uint32_t *V = reinterpret_cast<uint32_t *>(im.J);
-    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.ntiles; t += nw) {
-        const int ty = (int)(t / im.tiles_x), tx = (int)(t % im.tiles_x);
-        const int y0 = ty * WTH, x0 = tx * WTW;
+    for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nstrips; u += nw) {
+        const int uy = (int)(u / im.tiles_x), ux = (int)(u % im.tiles_x);
+        const int y0 = uy * WTH, x0 = ux * WTW;
         bool any = false, bad = false;
         for (int r = 0; r < WTH; r++) {
             const int y = y0 + r;
@@ -305,24 +377,31 @@ __global__ void __launch_bounds__(256) ws_init_kernel(EngineArgs a, WsArgs w) {
         bad = __any_sync(0xffffffffu, bad);
         __threadfence();
         if (lane == 0 && bad) set_status(a.hdr, kErrArg);
-        if (lane == 0 && any) notify_tile(a, t);
+        if (lane == 0 && any) notify_tile(a, (uint32_t)((uy / WSW) * im.tiles_x + ux));
     }
 }
 
 template <int CONN>
-__global__ void __launch_bounds__(kThreads, 2) ws_drain_kernel(EngineArgs a, WsArgs w) {
+__global__ void __launch_bounds__(kThreads, 2) ws_drain_kernel(EngineArgs a, WsArgs wa) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *wsmem = smem_raw + warp * kWsSmemPerWarp;
+    WsShared &C = *reinterpret_cast<WsShared *>(smem_raw + WSW * kWsSmemPerWarp);
     VisitStats st = {0, 0, 0, 0};
     unsigned long long idle = 0, busy = 0;
     for (;;) {
-        bool first;
-        const uint32_t t = acquire_tile(a, first, idle, lane);
+        if (warp == 0) {
+            bool first;
+            const uint32_t t = acquire_tile(a, first, idle, lane);
+            if (lane == 0) C.tile = t;
+        }
+        __syncthreads();
+        const uint32_t t = C.tile;
         if (t == kDone) break;
         const unsigned long long b0 = globaltimer_ns();
-        ws_visit<CONN>(a, w, t, wsmem, st, lane);
-        busy += globaltimer_ns() - b0;
+        ws_visit<CONN>(a, wa, t, wsmem, C, st, warp, lane);
+        if (warp == 0) busy += globaltimer_ns() - b0;
+        __syncthreads();   // every warp has read C.tile before the next pop overwrites it
     }
     flush_stats(a, st, idle, busy, lane);
 }
@@ -338,18 +417,20 @@ __global__ void ws_finish_kernel(uint32_t *V, int32_t *levels, size_t n) {
 
 struct WsLayout {
     size_t state, queue, total;
-    uint32_t ntiles;
+    uint32_t ntiles, nstrips;   // 64 x 64 CTA tiles; 16 x 64 strips
     int tiles_x, tiles_y;
 };
 
 bool ws_layout(int64_t H, int64_t W, WsLayout &L) {
     if (H < 1 || W < 1 || H >= (1ll << 31) || W >= (1ll << 31) || (uint64_t)H * (uint64_t)W >= (1ull << 40))
         return false;
-    const uint64_t tx = (uint64_t)((W + WTW - 1) / WTW), ty = (uint64_t)((H + WTH - 1) / WTH);
-    if (tx * ty >= (1ull << 31)) return false;
+    const uint64_t tx = (uint64_t)((W + WTW - 1) / WTW), ty = (uint64_t)((H + WCH - 1) / WCH);
+    const uint64_t sy = (uint64_t)((H + WTH - 1) / WTH);
+    if (tx * sy >= (1ull << 31)) return false;
     L.tiles_x = (int)tx;
     L.tiles_y = (int)ty;
     L.ntiles = (uint32_t)(tx * ty);
+    L.nstrips = (uint32_t)(tx * sy);
     L.state = 256;
     L.queue = L.state + align256((size_t)L.ntiles * 4);
     L.total = L.queue + align256((size_t)L.ntiles * 4);
@@ -400,17 +481,16 @@ extern "C" int iwpp_watershed(const uint32_t *markers, const void *gradient, int
     if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4, s) != cudaSuccess) return IWPP_ERR_CUDA;
     const int sms = device_sm_count();
     if (sms <= 0) return IWPP_ERR_CUDA;
-    uint32_t ig = (L.ntiles + 7) / 8;
+    uint32_t ig = (L.nstrips + 7) / 8;
     if (ig > (uint32_t)sms * 8) ig = (uint32_t)sms * 8;
-    ws_init_kernel<<<ig, 256, 0, s>>>(a, w);
-    const size_t smem = kWsSmemPerWarp * kWarpsPerCta;
+    ws_init_kernel<<<ig, 256, 0, s>>>(a, w, L.nstrips);
+    const size_t smem = kWsSmemCta;
     void (*drain)(EngineArgs, WsArgs) = connectivity == 8 ? ws_drain_kernel<8> : ws_drain_kernel<4>;
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, drain, kThreads, smem) != cudaSuccess || bps < 1)
         return IWPP_ERR_CUDA;
     long long g = (long long)bps * sms;
-    const long long need = ((long long)L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
-    if (g > need) g = need;
+    if (g > (long long)L.ntiles) g = L.ntiles;   // one CTA per tile
     drain<<<(int)g, kThreads, smem, s>>>(a, w);
     const size_t n = (size_t)H * (size_t)W;
     ws_finish_kernel<<<sms * 8, 256, 0, s>>>(labels_out, levels_out, n);

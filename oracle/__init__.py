@@ -57,32 +57,36 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(lib):
+    """Declare the C functions' signatures on a loaded oracle library."""
+    lib.oracle_reconstruct.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_reconstruct.restype = ctypes.c_int
+    lib.oracle_precondition_ok.argtypes = [ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_int]
+    lib.oracle_precondition_ok.restype = ctypes.c_int
+    lib.oracle_edt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_edt.restype = ctypes.c_int
+    lib.oracle_watershed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                     ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_watershed.restype = ctypes.c_int
+    lib.oracle_skiz.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+    lib.oracle_skiz.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB)
-            lib.oracle_reconstruct.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
-                                               ctypes.c_int64, ctypes.c_int, ctypes.c_int,
-                                               ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
-            lib.oracle_reconstruct.restype = ctypes.c_int
-            lib.oracle_precondition_ok.argtypes = [ctypes.c_void_p, ctypes.c_void_p,
-                                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
-                                                   ctypes.c_int]
-            lib.oracle_precondition_ok.restype = ctypes.c_int
-            lib.oracle_edt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
-            lib.oracle_edt.restype = ctypes.c_int
-            lib.oracle_watershed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
-                                             ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                             ctypes.POINTER(ctypes.c_uint64)]
-            lib.oracle_watershed.restype = ctypes.c_int
-            lib.oracle_skiz.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
-                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
-            lib.oracle_skiz.restype = ctypes.c_int
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
 
 

@@ -500,9 +500,10 @@ IWPP_API int iwpp_edt(const void *mask, uint32_t *site_out, uint32_t *dist2_out,
 
 /*
  * Work counters of the last call (single image or batch) that used `workspace`: tile
- * visits by the persistent kernel, wave-queue entries processed (pops),
- * entries created by the visits' initial scans (seeds), wave steps run (row
- * passes for the register solver), and
+ * visits by the persistent kernel (CTA-tile visits for the cooperative solver),
+ * wave-queue entries processed (pops), entries created by the visits' initial
+ * scans (seeds), wave steps run (row passes for the register solver, summed over
+ * the strips for the cooperative one), and
  * the persistent workers' summed waiting time and processing time in ns.
  * Host pointer out[6]. Synchronises `stream`. Returns IWPP_OK or IWPP_ERR_CUDA.
  */

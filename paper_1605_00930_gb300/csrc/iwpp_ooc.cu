@@ -15,9 +15,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <vector>
 
 #include "../../include/iwpp.h"
+#include "iwpp_bands.h"
 #include "iwpp_host.h"
 
 namespace iwpp {
@@ -127,38 +127,22 @@ extern "C" int iwpp_reconstruct_host(void *marker_inout, const void *mask, int64
     };
 
     // A band is a fixed point given its halo rows once reconstructed; it needs another visit
-    // only when a neighbour band changed afterwards (its halo rows may then differ). Bands
-    // are visited top to bottom, then bottom to top, skipping clean ones, until none is dirty.
-    std::vector<char> dirty((size_t)nb, 1);
-    int64_t ndirty = nb;
+    // only when a neighbour band changed afterwards (iwpp_bands.h).
+    BandSchedule order(nb);
     int32_t visits = 0;
-    bool down = true;
-    while (ndirty > 0) {
-        for (int64_t k = 0; k < nb; k++) {
-            const int64_t b = down ? k : nb - 1 - k;
-            if (!dirty[(size_t)b]) continue;
-            if (cudaMemsetAsync(acc + 1, 0, 4, s) != cudaSuccess) return IWPP_ERR_CUDA;
-            const int rc = do_band(b);
-            if (rc != IWPP_OK) return rc;
-            uint32_t h[2] = {0, 0};
-            if (cudaMemcpyAsync(h, acc, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return IWPP_ERR_CUDA;
-            if (cudaStreamSynchronize(s) != cudaSuccess) return IWPP_ERR_CUDA;
-            visits++;
-            dirty[(size_t)b] = 0;
-            ndirty--;
-            if (h[0] != 0) {
-                if (visits_out) *visits_out = visits;
-                return (int)h[0];
-            }
-            if (h[1]) {
-                for (int64_t nbr : {b - 1, b + 1})
-                    if (nbr >= 0 && nbr < nb && !dirty[(size_t)nbr]) {
-                        dirty[(size_t)nbr] = 1;
-                        ndirty++;
-                    }
-            }
+    for (int64_t b = order.next(); b >= 0; b = order.next()) {
+        if (cudaMemsetAsync(acc + 1, 0, 4, s) != cudaSuccess) return IWPP_ERR_CUDA;
+        const int rc = do_band(b);
+        if (rc != IWPP_OK) return rc;
+        uint32_t h[2] = {0, 0};
+        if (cudaMemcpyAsync(h, acc, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return IWPP_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return IWPP_ERR_CUDA;
+        visits++;
+        if (h[0] != 0) {
+            if (visits_out) *visits_out = visits;
+            return (int)h[0];
         }
-        down = !down;
+        order.visited(b, h[1] != 0);
     }
     if (visits_out) *visits_out = visits;
     return IWPP_OK;

@@ -44,6 +44,29 @@ def test_library_exports_every_declared_symbol(iwpp):
     assert set(_declared()) <= set(iwpp.exported_symbols())
 
 
+def test_header_constants_match_the_binding(iwpp):
+    """The binding's enum values and plan layout are the header's (parsed as text)."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "iwpp.h")).read()
+
+    def enum_value(name):
+        m = re.search(r"\b" + name + r"\s*=\s*(\d+)", hdr)
+        assert m, name
+        return int(m.group(1))
+
+    for name in ("IWPP_U8", "IWPP_U16", "IWPP_DILATE", "IWPP_ERODE", "IWPP_SOLVER_QUEUE",
+                 "IWPP_SOLVER_REGISTER", "IWPP_SOLVER_COOP"):
+        assert getattr(iwpp, name) == enum_value(name), name
+    for code, name in iwpp.STATUS.items():
+        assert enum_value(name) == code, name
+    body = hdr[hdr.index("typedef struct {\n    int32_t tile_h"):]
+    body = body[:body.index("} iwpp_plan;")]
+    fields = re.findall(r"(?:int32_t|int64_t|uint16_t)\s+([a-z_]+(?:,\s*[a-z_]+)*)", body)
+    names = [n.strip() for f in fields for n in f.split(",")]
+    assert names == [f for f, _ in iwpp.Plan._fields_]
+
+
 def test_default_plan_and_shapes(iwpp):
     p = iwpp.iwpp_default_plan()
     assert iwpp.iwpp_tile_shape_supported(p.tile_h, p.tile_w)

@@ -92,7 +92,7 @@ def test_random_small(iw, oracle_lib, shape, dtype, op, conn, solver):
         check(iw, oracle_lib, marker, mask, conn, op, p)
 
 
-# Widths around the 64-column register tile and its 2-pixel pairs (odd widths take the
+# Widths around the 64-column register tiles and strips and their 2-pixel pairs (odd widths take the
 # unaligned load path), heights around its 16 rows.
 EDGE_SHAPES = [(15, 63), (16, 64), (17, 65), (33, 127), (31, 128), (16, 129), (2, 2), (3, 1), (1, 3)]
 
@@ -101,7 +101,7 @@ EDGE_SHAPES = [(15, 63), (16, 64), (17, 65), (33, 127), (31, 128), (16, 129), (2
 @pytest.mark.parametrize("shape", EDGE_SHAPES + [(63, 65), (64, 64), (65, 130), (129, 63)])
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 @pytest.mark.parametrize("op", ["dilate", "erode"])
-def test_register_solver_edges(iw, oracle_lib, shape, dtype, op, solver):
+def test_strip_solver_edges(iw, oracle_lib, shape, dtype, op, solver):
     rng = np.random.default_rng([102, shape[0], shape[1], op == "erode"])
     p = _plan(iw, **SOLVERS[solver])
     for conn in (4, 8):

@@ -3,7 +3,8 @@ against a simulated image on the CPU. The simulation is the column form of the p
 1-D reconstruction J <- min(I, max(J(r-1), J(r), J(r+1))) over N rows, cut into bands that are
 solved with their neighbour rows as fixed sources, exactly as iwpp_reconstruct_host solves
 its bands on the device. When the schedule says no band is left to visit, the banded result
-must equal the reconstruction of the whole column (and every band must have been visited)."""
+must equal the reconstruction of the whole column (and every band must have been visited),
+also when a run is interrupted after any band and repeated on the partly processed rows."""
 import os
 import subprocess
 
@@ -45,14 +46,23 @@ int main() {
         std::vector<int> R = J;
         solve(R, I, 0, n);                       // the whole column at once
         const int nb = (n + band - 1) / band;
-        iwpp::BandSchedule order(nb);
+        // odd trials are interrupted after a few band visits and resumed with a fresh
+        // schedule on the partly processed rows (what repeating an interrupted call does)
+        const long stop_after = (trial & 1) ? (long)(rnd() % (2 * nb + 1)) : -1;
         std::vector<int> seen(nb, 0);
         long visits = 0;
-        for (long b = order.next(); b >= 0; b = order.next()) {
-            const int a = (int)b * band, e = std::min(n, a + band);
-            order.visited(b, solve(J, I, a, e));
-            seen[b] = 1;
-            if (++visits > 100000) { printf("no termination\n"); return 1; }
+        for (int pass = 0; pass < 2; pass++) {
+            iwpp::BandSchedule order(nb);
+            long here = 0;
+            for (long b = order.next(); b >= 0; b = order.next()) {
+                if (pass == 0 && stop_after >= 0 && here == stop_after) break;
+                const int a = (int)b * band, e = std::min(n, a + band);
+                order.visited(b, solve(J, I, a, e));
+                seen[b] = 1;
+                here++;
+                if (++visits > 100000) { printf("no termination\n"); return 1; }
+            }
+            if (stop_after < 0) break;
         }
         for (int b = 0; b < nb; b++)
             if (!seen[b]) { printf("band %d never visited\n", b); return 1; }

@@ -411,7 +411,9 @@ IWPP_API int iwpp_regional_maxima(const void *image, void *scratch, uint8_t *out
  *                        plane and a single-image workspace for band_rows + 2 rows
  *   visits_out           host int32 or NULL: band reconstructions made
  * Returns IWPP_OK, a host-detected error, or the first device error of any band (e.g.
- * IWPP_ERR_PRECONDITION; the host image is then unspecified).
+ * IWPP_ERR_PRECONDITION; the host image is then unspecified). Resumable: every pixel written
+ * back lies between the marker and the reconstruction, so if a call with a valid marker is
+ * interrupted at any point, repeating it on the same host buffers completes the result.
  */
 IWPP_API size_t iwpp_host_workspace_bytes(int64_t H, int64_t W, int dtype, int64_t band_rows);
 IWPP_API int iwpp_reconstruct_host(void *marker_inout, const void *mask, int64_t H, int64_t W, int connectivity,

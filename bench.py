@@ -1,13 +1,21 @@
 """Benchmark: Gpixels/s of bit-exact morphological reconstruction on GB300.
 
-Default workload (one step): the 4096 x 4096 u8 tissue-like blob field (2000 blobs,
-h-dome marker h = 30), reconstructed by dilation with 8- and with 4-connectivity
-(2 x 16.8 Mpx per step). Inputs are seeded synthetic data; the working set fits in
-L2, so L2 is flushed (256 MiB write) before every timed step, and the marker is
-restored by a device copy, both outside the timed events.
+Default workload (one step): the 512-image uneven batch (sides log-uniform in
+256..4096, u8 / u16 with p = 1/2, the first half h-dome dilations, the second half
+fill-holes, 8-connectivity; 970 Mpx), reconstructed as "batched + learned": the
+learned work estimator orders the batch's tiles (features, MLP, counting sort) and
+one persistent launch reconstructs every image, both replayed from CUDA graphs.
+Inputs are seeded synthetic data resident in HBM; markers are restored by a device
+copy and L2 is flushed (256 MiB write) before every timed step, both outside the
+timed events. The same line reports, on the same images, the plain per-image loop
+(one iwpp_reconstruct call per image) and the batched static form, the dominant
+kernel's roofline, an end-to-end number through the C ABI from pinned host buffers,
+and the CPU oracle on the host's cores; `forms` repeats the three forms on the other
+four workloads (512^2 noise blur, 4096^2 tissue with conn 8 and 4, the 16384^2
+sparse-seed image, the 256-image batch).
 
 Prints ONE JSON line (rank 0). `--impl reference` times the CPU oracle (Vincent's
-hybrid, single-threaded C) on the same workload instead.
+hybrid in C, one image per host thread) on the same workload instead.
 """
 from __future__ import annotations
 
@@ -40,24 +48,38 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _workload(name: str):
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+# ---- the five workloads -------------------------------------------------------------------
+WORKLOADS = {
+    "noiseblur512": "C1: noise-blur 512x512 u8 (5x5 box mean of uniform noise), marker = mask-40, dilation conn 8",
+    "tissue4096": ("C2: tissue 4096x4096 u8 (2000 blobs r 5-40, peak 80-255, over U{0..30} noise), h-dome "
+                   "marker h=30, dilation with conn 8 and with conn 4 (2 images)"),
+    "seeds16384": ("C3: blob field 16384x16384 u8 (2000 blobs), marker 0 except 1000 seed pixels equal to "
+                   "the mask, dilation conn 8"),
+    "batch256": ("C4: 256 images, sides log-uniform 256-4096, u8/u16, first half h-dome dilation "
+                 "(h 10-60), second half fill-holes (erosion), conn 8"),
+    "batch512": ("C5: 512 images generated like C4 (another seed stream), the learned schedule's test "
+                 "batch; estimator trained on 50k 64x64 blocks from runs of C1-C3"),
+}
+
+
+def load_workload(name: str):
     from paper_1605_00930_gb300 import synth
+    if name == "noiseblur512":
+        return [synth.noise_blur_case()]
     if name == "tissue4096":
         c = synth.tissue_case()
-        cases = [(c.marker, c.mask, 8, "dilate"), (c.marker, c.mask, 4, "dilate")]
-        desc = ("tissue 4096x4096 u8: 2000 blobs (r 5-40, peak 80-255) over U{0..30} noise, "
-                "h-dome marker h=30, dilation with conn 8 and conn 4")
-    elif name == "noiseblur512":
-        c = synth.noise_blur_case()
-        cases = [(c.marker, c.mask, 8, "dilate")]
-        desc = "noise-blur 512x512 u8, marker = mask-40, dilation conn 8"
-    elif name == "seeds16384":
-        c = synth.sparse_seed_case()
-        cases = [(c.marker, c.mask, 8, "dilate")]
-        desc = "blob field 16384x16384 u8, 2000 blobs, 1000 seed pixels, dilation conn 8"
-    else:
-        raise SystemExit(f"unknown workload {name}")
-    return cases, desc
+        return [c, synth.Case(c.marker, c.mask, 4, "dilate")]
+    if name == "seeds16384":
+        return [synth.sparse_seed_case()]
+    if name == "batch256":
+        return synth.mixed_batch(256, workload_id=4, workers=min(16, host_cores()))
+    if name == "batch512":
+        return synth.mixed_batch(512, workload_id=5, workers=min(16, host_cores()))
+    raise SystemExit(f"unknown workload {name}")
 
 
 class ClockSampler:
@@ -125,16 +147,17 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profiles(kernel: str):
-    """ncu DRAM bytes per launch recorded under profiles/ for the current kernel sources."""
+def _traffic_from_profiles(kernel: str, workload: str):
+    """ncu DRAM bytes per launch recorded under profiles/ for this kernel, workload and the
+    current kernel sources (None when there is no such record)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     digest = kernel_digest()
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
-            return float(parts[2])
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == digest:
+            return float(parts[3])
     return None
 
 
@@ -154,71 +177,334 @@ def job_gpx_s(world: int, pix_per_step: int, ms_per_step: float) -> float:
     return world * pix_per_step / (ms_per_step * 1e-3) / 1e9
 
 
+def _align(x: int, a: int = 256) -> int:
+    return (x + a - 1) // a * a
+
+
+class DeviceBatch:
+    """A workload's images in two device arenas (markers, masks; each image at a 256-byte
+    aligned offset) plus a copy of the initial markers, so that restoring every marker is
+    one device copy and host <-> device transfers are one copy per arena."""
+
+    def __init__(self, cases, dev):
+        import torch
+        self.cases = cases
+        self.offs, total = [], 0
+        for c in cases:
+            self.offs.append(total)
+            total += _align(c.mask.nbytes)
+        self.nbytes = total
+        host = np.zeros(total, np.uint8)
+        hmask = np.zeros(total, np.uint8)
+        for c, o in zip(cases, self.offs):
+            host[o:o + c.mask.nbytes] = c.marker.reshape(-1).view(np.uint8)
+            hmask[o:o + c.mask.nbytes] = c.mask.reshape(-1).view(np.uint8)
+        self.host_marker, self.host_mask = host, hmask
+        self.init = torch.from_numpy(host).to(dev)
+        self.marker = self.init.clone()
+        self.mask = torch.from_numpy(hmask).to(dev)
+        self.items = [(self.view(self.marker, i), self.view(self.mask, i), c.conn, c.op)
+                      for i, c in enumerate(cases)]
+        self.pixels = sum(int(c.mask.size) for c in cases)
+        self.alg_bytes = 3 * sum(int(c.mask.nbytes) for c in cases)   # read J, read I, write J
+
+    def view(self, arena, i):
+        import torch
+        c, o = self.cases[i], self.offs[i]
+        t = arena[o:o + c.mask.nbytes]
+        return (t.view(torch.uint16) if c.mask.dtype == np.uint16 else t).view(c.mask.shape)
+
+    def restore(self):
+        self.marker.copy_(self.init)
+
+    def outputs(self):
+        """Host copies of every image's current marker (the results after a run)."""
+        h = self.marker.cpu().numpy()
+        return [h[o:o + c.mask.nbytes].view(c.mask.dtype).reshape(c.mask.shape)
+                for c, o in zip(self.cases, self.offs)]
+
+
+def _capture(fn):
+    """A CUDA graph of fn(stream), captured on a side stream."""
+    import torch
+    cur = torch.cuda.current_stream()
+    s = torch.cuda.Stream()
+    s.wait_stream(cur)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            fn(s)
+    cur.wait_stream(s)
+    return g
+
+
+class Forms:
+    """The three forms of one workload on one DeviceBatch: plain per-image loop, batched
+    static (tile-id order), batched + learned schedule. Each batched form is two graphs
+    (prepare + scan, then the persistent drain) so that the drain can be timed alone."""
+
+    def __init__(self, db, sch, plan, dev):
+        from paper_1605_00930_gb300 import iwpp
+        self.db, self.sch, self.plan, self.dev = db, sch, plan, dev
+        self.Rs = [iwpp.Reconstructor(m.shape[0], m.shape[1], m.dtype, None, dev) for m, _, _, _ in db.items]
+        self.Bs = iwpp.Batch(db.items, plan)
+        self.Bl = iwpp.Batch(db.items, plan)
+        import torch
+        stream = torch.cuda.current_stream()
+        # one uncaptured call of each form first (kernel attributes, schedule buffers)
+        self.Bs(stream=stream)
+        self.order, self.sweeps = sch.schedule(self.Bl, stream) if sch is not None else (None, None)
+        self.Bl(order=self.order, sweeps=self.sweeps, stream=stream)
+        torch.cuda.synchronize()
+        db.restore()
+        self.g = {
+            "batched_static": (_capture(lambda s: self._scan(self.Bs, None, s)),
+                               _capture(lambda s: self._drain(self.Bs, None, s))),
+            "batched_learned": (_capture(lambda s: self._scan(self.Bl, sch, s)),
+                                _capture(lambda s: self._drain(self.Bl, sch, s))),
+        }
+
+    def _scan(self, B, sch, s):
+        if sch is not None:
+            sch.schedule(B, s)
+            rc = B.phase("scan", order=self.order, sweeps=self.sweeps, stream=s)
+        else:
+            rc = B.phase("scan", stream=s)
+        if rc != 0:
+            raise RuntimeError(f"batch scan phase failed: {rc}")
+
+    def _drain(self, B, sch, s):
+        rc = B.phase("drain", order=self.order if sch is not None else None,
+                     sweeps=self.sweeps if sch is not None else None, stream=s)
+        if rc != 0:
+            raise RuntimeError(f"batch drain phase failed: {rc}")
+
+    def plain(self, stream):
+        for R, (m, I, conn, op) in zip(self.Rs, self.db.items):
+            if R(m, I, conn, op, stream) != 0:
+                raise RuntimeError("plain call failed")
+
+    def launches(self, form: str) -> int:
+        """Kernel launches of the library in one step of `form`."""
+        from paper_1605_00930_gb300 import iwpp
+        n = len(self.db.items)
+        if form == "plain":
+            return 2 * n
+        sched = ((n + 31) // 32 + 5) if form == "batched_learned" else 0
+        return sched + iwpp.iwpp_batch_launch_count(n, 3)
+
+    def run(self, form: str, flush, ev=None):
+        """One step of `form` on the current stream (events: start, after scan, end)."""
+        import torch
+        stream = torch.cuda.current_stream()
+        if ev is not None:
+            ev[0].record(stream)
+        if form == "plain":
+            self.plain(stream)
+            if ev is not None:
+                ev[1].record(stream)
+        else:
+            gs, gd = self.g[form]
+            gs.replay()
+            if ev is not None:
+                ev[1].record(stream)
+            gd.replay()
+        if ev is not None:
+            ev[2].record(stream)
+
+    def status(self, form: str) -> int:
+        import torch
+        stream = torch.cuda.current_stream()
+        if form == "plain":
+            return max(R.status(stream) for R in self.Rs)
+        return (self.Bs if form == "batched_static" else self.Bl).status(stream)
+
+    def timed(self, form: str, flush, reps: int):
+        """Per-rep (total ms, drain ms), markers restored and L2 flushed before each rep."""
+        import torch
+        out = []
+        for _ in range(reps):
+            self.db.restore()
+            flush.fill_(1)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            self.run(form, flush, ev)
+            torch.cuda.synchronize()
+            out.append((ev[0].elapsed_time(ev[2]), ev[1].elapsed_time(ev[2])))
+        st = self.status(form)
+        if st != 0:
+            from paper_1605_00930_gb300 import iwpp
+            raise RuntimeError(f"{form}: device status {iwpp.STATUS.get(st, st)}")
+        return out
+
+
+def _stats(ts):
+    a = np.asarray(ts, dtype=np.float64)
+    med = float(np.median(a))
+    return med, (float(a.std() / a.mean()) if a.size > 1 and a.mean() > 0 else 0.0)
+
+
+def drain_kernel_name(db, plan) -> str:
+    """Name of the persistent kernel a batch call of this workload launches."""
+    from paper_1605_00930_gb300 import iwpp
+    kinds = {(c.mask.dtype.itemsize, c.conn) for c in db.cases}
+    solver = {iwpp.IWPP_SOLVER_QUEUE: "drain_kernel", iwpp.IWPP_SOLVER_REGISTER: "drain_reg_kernel",
+              iwpp.IWPP_SOLVER_COOP: "drain_coop_kernel"}[plan.local_solver]
+    if len(kinds) == 1:
+        (size, conn), = kinds
+        return f"{solver}<{'u16' if size == 2 else 'u8'}, {conn}>"
+    conns = {k[1] for k in kinds}
+    if plan.local_solver == iwpp.IWPP_SOLVER_COOP and len(conns) == 1:
+        return f"{solver}<u8|u16, {conns.pop()}>"
+    return f"{solver}<mixed>"
+
+
+def measure_forms(name, db, sch, plan, dev, flush, reps, peak):
+    """Plain, batched static and batched + learned on one workload: median time and CV over
+    `reps`, Gpx/s, the drain kernel's HBM fraction of the compulsory 3 s bytes per pixel,
+    and every form's output compared with the plain form's."""
+    import torch
+    F = Forms(db, sch, plan, dev)
+    res = {"workload": WORKLOADS[name], "images": len(db.items), "pixels": db.pixels,
+           "plan": plan.as_dict(), "drain_kernel": drain_kernel_name(db, plan)}
+    ref = None
+    for form in ("plain", "batched_static", "batched_learned"):
+        ts = F.timed(form, flush, reps)
+        med, cv = _stats([t[0] for t in ts])
+        dmed, _ = _stats([t[1] for t in ts])
+        out = db.marker.clone()
+        if ref is None:
+            ref = out
+            same = True
+        else:
+            same = bool(torch.equal(out, ref))
+        r = {"ms": round(med, 4), "cv": round(cv, 4), "gpx_s": round(db.pixels / med / 1e6, 3),
+             "same_output_as_plain": same, "launches_per_step": F.launches(form)}
+        if form != "plain":
+            ach = db.alg_bytes / (dmed * 1e-3) / 1e9
+            r.update({"drain_ms": round(dmed, 4), "drain_hbm_gbs": round(ach, 1),
+                      "drain_frac": round(ach / peak, 5)})
+        res[form] = r
+    for form in ("batched_static", "batched_learned"):
+        res[form]["speedup_vs_plain"] = round(res["plain"]["ms"] / res[form]["ms"], 3)
+    return res, F
+
+
+def oracle_check(cases, gpu_outputs, threads):
+    """Every image reconstructed by the CPU oracle on `threads` host threads and compared
+    pixel for pixel with the GPU's result. Returns (all equal, seconds)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    outs = oracle.reconstruct_many([(c.marker, c.mask, c.conn, c.op) for c in cases], threads=threads)
+    dt = time.perf_counter() - t0
+    return all(np.array_equal(o, g) for o, g in zip(outs, gpu_outputs)), dt
+
+
+def cpu_baseline(cases, gpu_outputs, threads):
+    """The oracle on the host's cores: the whole workload on `threads` threads (one image per
+    thread at a time; its outputs are also compared with the GPU's), and a one-core figure
+    on a strided sample of the images (about 5 s of work)."""
+    import oracle
+    oracle.build()
+    exact, dt = oracle_check(cases, gpu_outputs, threads)
+    px = sum(int(c.mask.size) for c in cases)
+    # one core: every k-th image, about 5 s at the N-core rate divided by N
+    budget_px = px / dt / threads * 5.0
+    k = max(1, int(round(px / max(budget_px, 1.0))))
+    sample = cases[::k]
+    t0 = time.perf_counter()
+    for c in sample:
+        oracle.reconstruct(c.marker, c.mask, c.conn, c.op)
+    dt1 = time.perf_counter() - t0
+    spx = sum(int(c.mask.size) for c in sample)
+    return {"value": round(px / dt / 1e9, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"the whole workload ({len(cases)} images, {px} px) on {threads} host threads, one "
+                       f"image per thread at a time, single-threaded C oracle per image"),
+            "seconds": round(dt, 2),
+            "one_core": {"value": round(spx / dt1 / 1e9, 5), "unit": UNIT, "cores": 1,
+                         "sample": f"every {k}-th image ({len(sample)} images, {spx} px) on one thread",
+                         "seconds": round(dt1, 2)},
+            "gpu_output_bit_exact": bool(exact)}
+
+
+def train_estimator(sets_cases, dev):
+    """The learned work estimator, trained on labels from runs of the given workloads."""
+    from paper_1605_00930_gb300 import learned
+    import torch
+    sets = []
+    for cases in sets_cases:
+        items = []
+        for c in cases:
+            items.append((torch.from_numpy(c.marker).to(dev), torch.from_numpy(c.mask).to(dev), c.conn, c.op))
+        sets.append(items)
+    t0 = time.time()
+    sch, report = learned.train_from_workloads(sets, n_samples=50000, epochs=60)
+    report["seconds"] = round(time.time() - t0, 2)
+    del sets
+    torch.cuda.empty_cache()
+    return sch, report
+
+
+def choose_plan(db, dev):
+    """The batch plan the library's autotuner picks on this workload (markers restored)."""
+    from paper_1605_00930_gb300 import iwpp
+    B = iwpp.Batch(db.items, iwpp.iwpp_default_batch_plan())
+    plan, _ = B.autotune(reps=2)
+    db.restore()
+    del B
+    return plan
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_1605_00930_gb300 import build as B
     B.build()
     from paper_1605_00930_gb300 import iwpp
 
+    full = rank == 0 and world == 1 and not args.quick
+    head_cases = load_workload(args.workload)   # generator processes start before any CUDA work
+    other = {}
+    if full:
+        for name in WORKLOADS:
+            if name != args.workload:
+                other[name] = load_workload(name)
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cases, desc = _workload(args.workload)
-    stream = torch.cuda.current_stream()
-    pix_per_step = sum(c[1].size for c in cases)
-    bytes_per_px = [c[1].dtype.itemsize for c in cases]
-
-    dev_cases = []
-    for marker, mask, conn, op in cases:
-        m0 = torch.from_numpy(marker).to(dev)
-        I = torch.from_numpy(mask).to(dev)
-        m = torch.empty_like(m0)
-        R = iwpp.Reconstructor(mask.shape[0], mask.shape[1], m0.dtype, None, dev)
-        dev_cases.append((m0, I, m, R, conn, op))
+    peak, peak_kind = _peaks()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step(ev=None):
-        for k, (m0, I, m, R, conn, op) in enumerate(dev_cases):
-            if ev is not None:
-                ev[k][0].record(stream)
-            rc = R.phase("scan", m, I, conn, op, stream)
-            if ev is not None:
-                ev[k][1].record(stream)
-            rc |= R.phase("drain", m, I, conn, op, stream)
-            if ev is not None:
-                ev[k][2].record(stream)
-            if rc != 0:
-                raise RuntimeError(iwpp.STATUS.get(rc))
+    # the learned estimator: labels from runs of the 512^2, 4096^2 (conn 8, 4) and 16384^2 workloads
+    def train_cases():
+        got = {n: (other.get(n) or (head_cases if n == args.workload else None))
+               for n in ("noiseblur512", "tissue4096", "seeds16384")}
+        return [got[n] if got[n] is not None else load_workload(n) for n in ("noiseblur512", "tissue4096", "seeds16384")]
+    sch, estimator = (None, None) if args.static else train_estimator(
+        [[c] for cs in train_cases() for c in cs], dev)
 
-    def prep():
-        for (m0, I, m, R, conn, op) in dev_cases:
-            m.copy_(m0)
-        flush.fill_(1)
+    db = DeviceBatch(head_cases, dev)
+    plan = choose_plan(db, dev)
+    forms, F = measure_forms(args.workload, db, sch, plan, dev, flush, max(3, args.form_reps), peak)
+    form = "batched_static" if sch is None else "batched_learned"
+    stream = torch.cuda.current_stream()
 
-    # one untimed run of the timed configuration; its output is compared with the CPU
-    # oracle's in the CPU-baseline leg below
-    prep()
-    step()
-    for (m0, I, m, R, conn, op) in dev_cases:
-        st = R.status(stream)
-        if st != 0:
-            raise RuntimeError(f"device status {iwpp.STATUS.get(st)}")
-    first_outputs = [m.cpu().numpy() for (m0, I, m, R, conn, op) in dev_cases]
     for _ in range(args.warmup):
-        prep()
-        step()
+        db.restore()
+        flush.fill_(1)
+        F.run(form, flush)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in dev_cases] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     gpu_index = dev.index
-    with ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(gpu_index)).split(",")[0])
-                      if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else gpu_index) as cs:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    with ClockSampler(int(vis) if vis.isdigit() else gpu_index) as cs:
         time.sleep(0.25)
         t0 = time.time()
         for i in range(args.steps):
-            prep()
-            step(evs[i])
+            db.restore()
+            flush.fill_(1)
+            F.run(form, flush, evs[i])
         torch.cuda.synchronize()
         t1 = time.time()
         if t1 - t0 < 0.3:
@@ -226,151 +512,111 @@ def run_ours(args, rank: int, world: int):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    scan_ms = sum(e[k][0].elapsed_time(e[k][1]) for e in evs for k in range(len(dev_cases)))
-    drain_ms = sum(e[k][1].elapsed_time(e[k][2]) for e in evs for k in range(len(dev_cases)))
-    total_ms = scan_ms + drain_ms
-    ms_per_step = total_ms / args.steps
-    ms_per_step = max_over_ranks(ms_per_step, world, dev)
-    value = job_gpx_s(world, pix_per_step, ms_per_step)
+    st = F.status(form)
+    if st != 0:
+        raise RuntimeError(f"device status {iwpp.STATUS.get(st, st)}")
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    drain_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ms_per_step = max_over_ranks(sum(step_ms) / args.steps, world, dev)
+    value = job_gpx_s(world, db.pixels, ms_per_step)
+    gpu_out = db.outputs()
+    head_arena = db.marker.cpu().numpy()
 
-    # end to end through the public call with host buffers
-    host_in = [(torch.from_numpy(c[0]).pin_memory(), torch.from_numpy(c[1]).pin_memory()) for c in cases]
-    host_out = [torch.empty_like(h[0]).pin_memory() for h in host_in]
-    h2d = sum(h[0].numel() * h[0].element_size() + h[1].numel() * h[1].element_size() for h in host_in)
-    d2h = sum(h.numel() * h.element_size() for h in host_out)
-
-    # one stream per call of the step (each call has its own device buffers and workspace),
-    # so one call's copies overlap the other call's kernels, as a user with streams would run it
-    e2e_streams = [torch.cuda.Stream(dev) for _ in dev_cases]
+    # end to end through the C ABI from pinned host buffers: per step the H2D copy of every
+    # marker and mask (two copies: the arenas), the learned schedule, the batch call, and the
+    # D2H copy of every result
+    hm = torch.from_numpy(db.host_marker).pin_memory()
+    hI = torch.from_numpy(db.host_mask).pin_memory()
+    ho = torch.empty_like(hm).pin_memory()
 
     def e2e_step():
-        for k, (m0, I, m, R, conn, op) in enumerate(dev_cases):
-            sk = e2e_streams[k]
-            with torch.cuda.stream(sk):
-                m.copy_(host_in[k][0], non_blocking=True)
-                I.copy_(host_in[k][1], non_blocking=True)
-                rc = R(m, I, conn, op, sk)
-                if rc != 0:
-                    raise RuntimeError(iwpp.STATUS.get(rc))
-                host_out[k].copy_(m, non_blocking=True)
+        db.marker.copy_(hm, non_blocking=True)
+        db.mask.copy_(hI, non_blocking=True)
+        if sch is not None:
+            order, sweeps = sch.schedule(F.Bl, stream)
+            rc = F.Bl(order=order, sweeps=sweeps, stream=stream)
+        else:
+            rc = F.Bs(stream=stream)
+        if rc != 0:
+            raise RuntimeError(f"batch call failed: {rc}")
+        ho.copy_(db.marker, non_blocking=True)
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
+    e2e_step()
     torch.cuda.synchronize()
-    n_e2e = max(3, min(args.steps, 50))
-    te0 = time.perf_counter()
-    for _ in range(n_e2e):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - te0) / n_e2e
-    for k, (m0, I, m, R, conn, op) in enumerate(dev_cases):
-        if R.status(e2e_streams[k]) != 0:
-            raise RuntimeError("device error in e2e run")
-        if not np.array_equal(host_out[k].numpy(), first_outputs[k]):
-            raise RuntimeError("end-to-end output differs from the device-resident run")
-
-    if rank != 0:
-        return None
-    peak, peak_kind = _peaks()
-    s = bytes_per_px[0]
-    nl = len(dev_cases)
-    plan = iwpp.iwpp_default_plan()
-    drain_name, scan_name = {iwpp.IWPP_SOLVER_QUEUE: ("drain_kernel", "scan_kernel"),
-                             iwpp.IWPP_SOLVER_REGISTER: ("drain_reg_kernel", "scan_reg_kernel"),
-                             iwpp.IWPP_SOLVER_COOP: ("drain_coop_kernel", "scan_coop_kernel")}[plan.local_solver]
-    dominant = drain_name if drain_ms >= scan_ms else scan_name
-    dom_ms = (drain_ms if dominant == drain_name else scan_ms) / (args.steps * nl)
-    alg_bytes = 3 * s * cases[0][1].size   # compulsory bytes of one reconstruction: read J, I, write J
-    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = _traffic_from_profiles(dominant)
-    cpu = cpu_baseline(cases, first_outputs) if rank == 0 and world == 1 and not args.no_cpu else None
-    forms = run_forms(args, dev) if rank == 0 and world == 1 and not args.quick else None
-    edt = run_edt(args, dev, peak) if rank == 0 and world == 1 and not args.quick else None
-    wshed = run_watershed(args, dev) if rank == 0 and world == 1 and not args.quick else None
-    skiz = run_skiz(args, dev) if rank == 0 and world == 1 and not args.quick else None
-    bands = run_host_bands(args, dev) if rank == 0 and world == 1 and not args.quick else None
-    out = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": desc, "pixels_per_step": pix_per_step, "form": "plain per-image",
-                   "plan": plan.as_dict(),
-                   "l2": "flushed before every timed step (256 MiB write)",
-                   "timing": "CUDA events around the scan and drain launches of each step",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "phases_ms_per_step": {scan_name: round(scan_ms / args.steps, 4),
-                               drain_name: round(drain_ms / args.steps, 4)},
-        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
-                     "traffic": traffic,
-                     "alg_bytes_per_launch": alg_bytes,
-                     "path_frac": round(3 * s * pix_per_step / (ms_per_step * 1e-3) / 1e9 / peak, 5)},
-        "e2e": {"value": round(world * pix_per_step / e2e_s / 1e9, 3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "form": "each call: pinned H2D of marker and mask, reconstruction, D2H of the result; "
-                        "one stream per call, steps back to back, wall clock over the steps"},
-        "gpu_launches": 2 * nl * args.steps,
-        "clocks": cs.summary(t0, t1),
-        "cpu_baseline": cpu,
-        "forms": forms,
-        "edt": edt,
-        "watershed": wshed,
-        "skiz": skiz,
-        "host_bands": bands,
-    }
-    return out
-
-
-def cpu_baseline(cases, gpu_outputs=None, budget_s: float = 12.0):
-    """Times the CPU oracle on the workload; its first pass is also compared, pixel for
-    pixel, with the GPU's untimed first run."""
-    import oracle
-    oracle.build()
-    done_px, t0 = 0, time.perf_counter()
-    reps = 0
-    exact = None
-    while True:
-        for k, (marker, mask, conn, op) in enumerate(cases):
-            r = oracle.reconstruct(marker, mask, conn, op)
-            if reps == 0 and gpu_outputs is not None:
-                exact = (exact is not False) and bool(np.array_equal(r, gpu_outputs[k]))
-            done_px += mask.size
-        reps += 1
-        if time.perf_counter() - t0 > budget_s or reps >= 5:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": round(done_px / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full pass(es) of the workload ({done_px} px), single-threaded C oracle",
-            "gpu_output_bit_exact": exact}
-
-
-def _dev_items(cases, dev):
-    import torch
-    items, init = [], []
-    for c in cases:
-        m0 = torch.from_numpy(c.marker).to(dev)
-        items.append((m0.clone(), torch.from_numpy(c.mask).to(dev), c.conn, c.op))
-        init.append(m0)
-    return items, init
-
-
-def _timed(run, items, init, flush, reps, stream):
-    """Median and all per-rep times (ms) of `run`, markers restored and L2 flushed
-    before every rep, CUDA events on `stream` around the run only."""
-    import torch
-    ts = []
-    for r in range(reps + 1):
-        for (m, _, _, _), m0 in zip(items, init):
-            m.copy_(m0)
+    e2e_ts = []
+    for _ in range(max(3, min(args.steps, 10))):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        run()
+        e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        if r > 0:
-            ts.append(e0.elapsed_time(e1))
-    return float(np.median(ts)), ts
+        e2e_ts.append(e0.elapsed_time(e1))
+    if F.status(form) != 0 or not np.array_equal(ho.numpy(), head_arena):
+        raise RuntimeError("end-to-end run failed or differs from the device-resident run")
+    e2e_ms = max_over_ranks(float(np.mean(e2e_ts)), world, dev)
+    if rank != 0:
+        return None
+
+    kname = drain_kernel_name(db, plan)
+    dmean = float(np.mean(drain_ms))
+    achieved = db.alg_bytes / (dmean * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/u16 (16-bit integer lanes)", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "images": len(head_cases),
+                   "pixels_per_step": db.pixels,
+                   "form": ("batched + learned schedule: features, MLP and tile order, then one persistent "
+                            "launch over every image; both replayed from CUDA graphs" if sch is not None else
+                            "batched, static tile order, CUDA graphs"),
+                   "plan": plan.as_dict(),
+                   "l2": "flushed before every timed step (256 MiB write); the inputs also exceed L2",
+                   "timing": "CUDA events on the launching stream around each step (schedule + batch call)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "plain": forms["plain"], "batched_static": forms["batched_static"],
+        "batched_learned": forms["batched_learned"],
+        "speedup_vs_plain": round(forms["plain"]["ms"] / ms_per_step, 3),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 5),
+                     "traffic": _traffic_from_profiles(kname, args.workload),
+                     "alg_bytes_per_launch": db.alg_bytes,
+                     "drain_ms_per_launch": round(dmean, 4),
+                     "path_frac": round(db.alg_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 5)},
+        "e2e": {"value": round(world * db.pixels / e2e_ms / 1e6, 3), "unit": UNIT,
+                "h2d_bytes_per_step": 2 * db.nbytes, "d2h_bytes_per_step": db.nbytes,
+                "ms_per_step": round(e2e_ms, 3),
+                "form": ("per step: pinned H2D of every marker and mask (two arena copies), the learned "
+                         "schedule and the batch call through the C ABI, D2H of every result; L2 flushed "
+                         "before each step; CUDA events around the step")},
+        "gpu_launches": F.launches(form) * args.steps,
+        "clocks": cs.summary(t0, t1),
+        "estimator": estimator,
+    }
+    if full:
+        other_out = {}
+        res_forms = {}
+        for name, cases in other.items():
+            d2 = DeviceBatch(cases, dev)
+            p2 = choose_plan(d2, dev)
+            r, F2 = measure_forms(name, d2, sch, p2, dev, flush, max(3, args.form_reps), peak)
+            other_out[name] = (cases, d2.outputs())
+            res_forms[name] = r
+            del F2, d2
+            torch.cuda.empty_cache()
+        out["forms"] = res_forms
+        out["edt"] = run_edt(args, dev, peak)
+        out["watershed"] = run_watershed(args, dev)
+        out["skiz"] = run_skiz(args, dev)
+        out["host_bands"] = run_host_bands(args, dev)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(head_cases, gpu_out, host_cores())
+        if full:
+            for name, (cases, outs) in other_out.items():
+                ok, dt = oracle_check(cases, outs, host_cores())
+                out["forms"][name]["oracle_bit_exact"] = ok
+                out["forms"][name]["oracle_seconds"] = round(dt, 2)
+    return out
 
 
 def run_edt(args, dev, peak):
@@ -568,151 +814,73 @@ def ctypes_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def run_forms(args, dev):
-    """Plain per-image form against the batched (one persistent CUDA-graph launch,
-    autotuned plan) and batched + learned-schedule forms, on the sparse-seed 16384^2
-    image, the 256-image uneven batch and the 512-image batch; outputs of every form
-    are checked equal to the plain form's."""
-    import torch
-    from paper_1605_00930_gb300 import iwpp, learned, synth
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    reps = max(1, args.form_reps)
-    out = {}
-    t_start = time.time()
-
-    # learned estimator: labels from runs of the 512^2, 4096^2 (conn 8 and 4) and 16384^2 workloads
-    c1, c2 = synth.noise_blur_case(), synth.tissue_case()
-    c2b = synth.Case(c2.marker, c2.mask, 4, "dilate")
-    c3 = synth.sparse_seed_case()
-    sets = [_dev_items([c], dev)[0] for c in (c1, c2, c2b, c3)]
-    t0 = time.time()
-    sch, report = learned.train_from_workloads(sets, n_samples=50000, epochs=60)
-    report["seconds"] = round(time.time() - t0, 2)
-    out["estimator"] = report
-    del sets
-
-    def plain_loop(items):
-        Rs = [iwpp.Reconstructor(m.shape[0], m.shape[1], m.dtype, None, dev) for m, _, _, _ in items]
-
-        def run():
-            for R, (m, I, conn, op) in zip(Rs, items):
-                if R(m, I, conn, op, stream) != 0:
-                    raise RuntimeError("plain call failed")
-        return run, Rs
-
-    def batched(items, plan, learned_sched):
-        B = iwpp.Batch(items, plan)
-        if learned_sched:
-            g = torch.cuda.CUDAGraph()
-            s = torch.cuda.Stream()
-            s.wait_stream(stream)
-            with torch.cuda.stream(s):
-                order, sweeps = sch.schedule(B, s)        # allocate the schedule buffers first
-                with torch.cuda.graph(g, stream=s):
-                    sch.schedule(B, s)
-                    if B(order=order, sweeps=sweeps, stream=s) != 0:
-                        raise RuntimeError("batch call failed")
-            stream.wait_stream(s)
-            return (lambda: g.replay()), B
-        G = B.graph()
-        return (lambda: G.launch(stream)), (B, G)
-
-    def compare(name, cases, tune):
-        items, init = _dev_items(cases, dev)
-        px = sum(c.mask.size for c in cases)
-        res = {"images": len(cases), "pixels": px}
-        run, keep = plain_loop(items)
-        ms, _ = _timed(run, items, init, flush, reps, stream)
-        ref = [m.cpu().numpy() for m, _, _, _ in items]
-        res["plain_ms"] = round(ms, 3)
-        res["plain_gpx_s"] = round(px / ms / 1e6, 3)
-        plan = iwpp.iwpp_default_batch_plan()
-        if tune:
-            for (m, _, _, _), m0 in zip(items, init):   # tune on the inputs, not on the result
-                m.copy_(m0)
-            Bt = iwpp.Batch(items, plan)
-            plan, tms = Bt.autotune(reps=2)
-            res["autotuned_plan"] = plan.as_dict()
-            del Bt
-        for form, lsch in (("batched_static", False), ("batched_learned", True)):
-            run, keep = batched(items, plan, lsch)
-            ms, _ = _timed(run, items, init, flush, reps, stream)
-            same = all(np.array_equal(m.cpu().numpy(), r) for (m, _, _, _), r in zip(items, ref))
-            res[form + "_ms"] = round(ms, 3)
-            res[form + "_gpx_s"] = round(px / ms / 1e6, 3)
-            res[form + "_same_output"] = bool(same)
-            res[form + "_speedup_vs_plain"] = round(res["plain_ms"] / ms, 3)
-            del keep
-        out[name] = res
-
-    compare("seeds16384", [c3], tune=True)
-    del c1, c2, c2b, c3
-    compare("batch256", synth.mixed_batch(256, workload_id=4), tune=True)
-    compare("batch512", synth.mixed_batch(512, workload_id=5), tune=True)
-    out["seconds"] = round(time.time() - t_start, 1)
-    return out
-
-
-
 REFERENCE_BUDGET_S = 120.0   # wall-clock target of the whole --impl reference run
 
 
 def run_reference(args, rank: int, world: int):
-    """The oracle arm: the single-threaded C oracle timed on the host, on the same workload,
-    metric and unit. A step of the full workload takes the oracle seconds, so when the
-    requested steps would not fit the time budget every step is a bounded sample: the same
-    calls on a band of the image's first rows (the same structure and value distribution),
-    sized from a timed first pass of the full workload."""
+    """The oracle arm: the C oracle (one image per host thread, on every core of the host)
+    timed on the same workload, metric and unit. When the requested steps of the whole
+    workload would not fit the time budget, every step is a bounded sample of it, sized from
+    a timed pass of the whole workload: every k-th image of a batch (the same mix of sizes,
+    pixel types, dilations and fill-holes), or the first rows of each image of a
+    single-image workload."""
     if rank != 0:
         return None
     import oracle
     oracle.build()
-    cases, desc = _workload(args.workload)
-    full_px = sum(c[1].size for c in cases)
+    cases = load_workload(args.workload)
+    threads = host_cores()
+    items = [(c.marker, c.mask, c.conn, c.op) for c in cases]
+    full_px = sum(int(c.mask.size) for c in cases)
     t0 = time.perf_counter()
-    for c in cases:
-        oracle.reconstruct(*c)
+    oracle.reconstruct_many(items, threads=threads)
     full_s = time.perf_counter() - t0
     nsteps = args.steps + max(0, args.warmup - 1)
-    rows = cases[0][1].shape[0]
+    sample_desc = f"every step is the whole workload ({len(items)} images, {full_px} px)"
     if nsteps * full_s > REFERENCE_BUDGET_S:
         frac = REFERENCE_BUDGET_S / (nsteps * full_s)
-        rows = max(16, int(rows * frac))
-        cases = [(np.ascontiguousarray(m[:rows]), np.ascontiguousarray(i[:rows]), conn, op)
-                 for (m, i, conn, op) in cases]
-    pix = sum(c[1].size for c in cases)
-    sample = (f"every step is the full workload ({full_px} px)" if pix == full_px else
-              f"every step: the first {rows} rows of each image ({pix} of {full_px} px; the full "
-              f"workload takes the oracle {full_s:.2f} s per step)")
+        if len(items) >= 8:
+            k = int(np.ceil(1.0 / frac))
+            items = items[::k]
+            sample_desc = f"every step: every {k}-th image"
+        else:
+            rows = max(16, int(cases[0].mask.shape[0] * frac))
+            items = [(np.ascontiguousarray(m[:rows]), np.ascontiguousarray(i[:rows]), conn, op)
+                     for (m, i, conn, op) in items]
+            sample_desc = f"every step: the first {rows} rows of each image"
+        spx = sum(int(it[1].size) for it in items)
+        sample_desc += (f" ({len(items)} images, {spx} of {full_px} px; the whole workload takes the oracle "
+                        f"{full_s:.2f} s on {threads} threads)")
+    pix = sum(int(it[1].size) for it in items)
     for _ in range(max(0, args.warmup - 1)):
-        for c in cases:
-            oracle.reconstruct(*c)
+        oracle.reconstruct_many(items, threads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for c in cases:
-            oracle.reconstruct(*c)
+        oracle.reconstruct_many(items, threads=threads)
     dt = (time.perf_counter() - t0) / args.steps
     value = pix / dt / 1e9
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": desc, "pixels_per_step": pix},
-            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample + ", single-threaded C oracle"},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/u16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "pixels_per_step": pix},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample_desc + "; single-threaded C oracle per image, one image per "
+                                                     "thread at a time"},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tissue4096", choices=["tissue4096", "noiseblur512", "seeds16384"])
+    ap.add_argument("--workload", default="batch512", choices=list(WORKLOADS))
+    ap.add_argument("--static", action="store_true", help="time the static schedule instead of the learned one")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--quick", action="store_true", help="skip the batched / learned comparisons")
-    ap.add_argument("--form-reps", type=int, default=5)
+    ap.add_argument("--quick", action="store_true", help="headline workload only (no other forms or operators)")
+    ap.add_argument("--form-reps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -94,8 +94,10 @@ typedef enum {
  *                      its four warps holds a 16-row strip as the register
  *                      solver does, and the strips exchange their boundary
  *                      rows through shared memory until the tile is settled
- *                      (tile_h == tile_w == 64, no sweeps, no value levels,
- *                      at most 5 CTAs per SM)
+ *                      (tile_h == tile_w == 64, no revisit sweeps, no value
+ *                      levels, at most 5 CTAs per SM; its scan kernel runs the
+ *                      sweep pairs on the whole 64 x 64 tile, the strips
+ *                      exchanging boundary rows after each pair)
  *   value_levels       0 or 1: the persistent kernel's tile queue is one FIFO;
  *                      2..16: one queue per value level, and a worker takes
  *                      its next tile from the highest level that has one (the
@@ -125,8 +127,8 @@ enum { IWPP_SOLVER_QUEUE = 0, IWPP_SOLVER_REGISTER = 1, IWPP_SOLVER_COOP = 2 };
  * 64 x 64 tiles, cooperative solver. Returns IWPP_OK. */
 IWPP_API int iwpp_default_plan(iwpp_plan *plan);
 
-/* Fills *plan with the static default schedule of batch calls (a NULL plan there): 16 x 64
- * tiles, register solver. Returns IWPP_OK. */
+/* Fills *plan with the static default schedule of batch calls (a NULL plan there): the
+ * single-image default (64 x 64 tiles, cooperative solver). Returns IWPP_OK. */
 IWPP_API int iwpp_default_batch_plan(iwpp_plan *plan);
 
 /* 1 if (tile_h, tile_w) is a compiled tile shape, else 0. */
@@ -232,6 +234,26 @@ IWPP_API int iwpp_reconstruct_batch_sched(const iwpp_image *imgs, int n, const i
                                           const uint32_t *tile_order, const uint8_t *tile_sweeps,
                                           uint32_t *tile_work, void *workspace, size_t ws_bytes,
                                           void *stream);
+
+/*
+ * One step of iwpp_reconstruct_batch_sched (Algorithm 6's two phases, for callers
+ * that time or overlap them separately): phases = 1 enqueues the image-table upload,
+ * the workspace reset, the scan kernel (precondition, sweeps, frontier) and the
+ * queue compaction; phases = 2 enqueues only the persistent drain, which reuses the
+ * workspace prepared by a phases = 1 call with identical arguments (same images,
+ * plan, schedule and workspace) earlier on the same stream; phases = 3 is the whole
+ * call. A phases = 1 call followed by a phases = 2 call is exactly
+ * iwpp_reconstruct_batch_sched. Other values: IWPP_ERR_ARG. Same arguments,
+ * ownership and errors otherwise.
+ */
+IWPP_API int iwpp_reconstruct_batch_phase(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                          const uint32_t *tile_order, const uint8_t *tile_sweeps,
+                                          uint32_t *tile_work, int phases, void *workspace, size_t ws_bytes,
+                                          void *stream);
+
+/* Kernel launches one iwpp_reconstruct_batch_phase call with n images makes (-1 for a
+ * bad argument). Host-only call. */
+IWPP_API int iwpp_batch_launch_count(int n, int phases);
 
 /*
  * ---- CUDA graphs and autotuning (host runtime) ----------------------------------
@@ -354,17 +376,26 @@ IWPP_API int iwpp_tile_work_to_blocks(const iwpp_image *imgs, int n, const iwpp_
  * cudaMalloc, cudaFree or other allocating routine. The caller passes the marker
  * (overwritten by the result) and the mask, as for iwpp_reconstruct.
  *   - Images whose workspace would exceed the array are rejected with
- *     IWPP_ERR_WORKSPACE before anything is enqueued (about 400 megapixels on a GB300;
- *     iwpp_workspace_bytes(H, W, dtype, NULL) gives the need).
+ *     IWPP_ERR_WORKSPACE before anything is enqueued. With the default plan the
+ *     workspace is about 8 bytes per 64 x 64 tile (a tile state and a queue slot) plus
+ *     1 KB, so the limit is about 1 M tiles, i.e. about 4.2 gigapixels;
+ *     iwpp_workspace_bytes(H, W, dtype, NULL) gives the exact need.
  *   - The first call on a device looks up the array's device address for that device
- *     (with that device current); make that first call before any stream capture.
+ *     (with that device current). Under CUDA's lazy module loading that first use is
+ *     also where the library's device code and this array are loaded onto the device,
+ *     which can allocate and synchronise: make the first call on each device outside
+ *     any timed region and before any stream capture.
  *   - Every call on a device shares the one array; each call resets the parts that must
  *     start at zero. Calls whose work overlaps on the GPU (other streams, other host
  *     threads) race on it and must be serialised by the caller.
  *   - status_out (may be NULL): when given, the call waits for `stream` and stores the
  *     device status (IWPP_OK or an iwpp_status code) there; otherwise the call is
- *     asynchronous and the device status is not reported.
- * Returns IWPP_OK or a host-detected error code.
+ *     asynchronous and the device status is not reported. A call made while `stream`
+ *     is being captured must pass NULL (waiting would end the capture): with a
+ *     non-NULL status_out it returns IWPP_ERR_ARG and enqueues nothing.
+ * Returns IWPP_OK or a host-detected error code: IWPP_ERR_ARG for a bad pointer,
+ * size, connectivity, op or dtype; IWPP_ERR_WORKSPACE for an image beyond the array;
+ * IWPP_ERR_CUDA when a CUDA call fails.
  */
 #define IWPP_NOALLOC_SCRATCH_BYTES (8u << 20)
 IWPP_API int iwpp_reconstruct_noalloc(void *marker_inout, const void *mask, int64_t H, int64_t W,
@@ -401,14 +432,17 @@ IWPP_API int iwpp_regional_maxima(const void *image, void *scratch, uint8_t *out
  * whose mask is set to their marker (fixed sources), reconstructed through the single-image
  * path, and copied back. Bands are visited top to bottom, then bottom to top, a band again
  * only after a neighbour band changed, until no band is left to visit: the result is
- * bit-identical to iwpp_reconstruct. Blocking: the call synchronises `stream` after every
- * band.
+ * bit-identical to iwpp_reconstruct. While a band is reconstructed on `stream`, the band
+ * expected next is copied to the device on a stream of the call's own (two band buffers).
+ * Blocking: the call waits for every band's change flag; it creates and destroys that
+ * stream, a few events and an 8-byte pinned host buffer.
  *   marker_inout, mask   HOST, H x W of `dtype`, row-major (pinned memory copies fastest);
  *                        the result overwrites marker_inout
  *   band_rows            rows per band, >= 1 (a band of >= H rows is one reconstruction)
  *   workspace            device, 256-byte aligned, iwpp_host_workspace_bytes(H, W, dtype,
- *                        band_rows) bytes: two (band_rows + 2) x W planes, one band_rows x W
- *                        plane and a single-image workspace for band_rows + 2 rows
+ *                        band_rows) bytes: two band buffers (each two (band_rows + 2) x W
+ *                        planes and one band_rows x W plane) and a single-image workspace
+ *                        for band_rows + 2 rows
  *   visits_out           host int32 or NULL: band reconstructions made
  * Returns IWPP_OK, a host-detected error, or the first device error of any band (e.g.
  * IWPP_ERR_PRECONDITION; the host image is then unspecified). Resumable: every pixel written

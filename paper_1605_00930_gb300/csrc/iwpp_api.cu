@@ -39,7 +39,9 @@ int shape_index(int th, int tw) {
 }
 
 // A scan / drain kernel pair with its shared-memory size function. Index [shape][v]:
-// v = 0..3 single-image kinds (bit 0 = u16, bit 1 = 8-connectivity), v = 4 mixed batch.
+// v = 0..3 single-image kinds (bit 0 = u16, bit 1 = 8-connectivity), v = 4 mixed batch,
+// v = 5 / 6 batches of one connectivity (4 / 8) with both pixel types (cooperative solver
+// only: its kernels read the pixel size from each image at run time).
 struct KernelSet {
     void (*scan)(EngineArgs);
     void (*drain)(EngineArgs);
@@ -47,7 +49,7 @@ struct KernelSet {
     RegKernelSet reg;                // register local solver (16 x 64 tiles), else null
     RegKernelSet coop;               // cooperative local solver (64 x 64 tiles), else null
 };
-static constexpr int kMixed = 4;
+static constexpr int kMixed = 4, kAnyPix4 = 5, kAnyPix8 = 6, kVariants = 7;
 
 template <typename T, int CONN, int TH, int TW>
 static KernelSet make_set() {
@@ -66,7 +68,7 @@ static size_t mixed_smem_bytes(uint32_t qcap) {
 }
 
 template <int TH, int TW>
-static void fill_shape(KernelSet (&row)[5]) {
+static void fill_shape(KernelSet (&row)[kVariants]) {
     row[0] = make_set<uint8_t, 4, TH, TW>();
     row[1] = make_set<uint16_t, 4, TH, TW>();
     row[2] = make_set<uint8_t, 8, TH, TW>();
@@ -76,10 +78,17 @@ static void fill_shape(KernelSet (&row)[5]) {
     row[kMixed].smem = &mixed_smem_bytes<TH, TW>;
     row[kMixed].reg = reg_kernel_set(TH, TW, kMixed);
     row[kMixed].coop = coop_kernel_set(TH, TW, kMixed);
+    for (int v : {kAnyPix4, kAnyPix8}) {
+        row[v].scan = nullptr;
+        row[v].drain = nullptr;
+        row[v].smem = nullptr;
+        row[v].reg = reg_kernel_set(TH, TW, v);
+        row[v].coop = coop_kernel_set(TH, TW, v);
+    }
 }
 
-static KernelSet g_sets[kNumShapes][5];
-static int g_smem_set[kNumShapes][5];
+static KernelSet g_sets[kNumShapes][kVariants];
+static int g_smem_set[kNumShapes][kVariants];
 static std::once_flag g_once;
 static std::mutex g_mu;
 
@@ -106,11 +115,8 @@ static cudaError_t ensure_smem_attr(int shape, int v, size_t bytes) {
     if ((size_t)done >= bytes) return cudaSuccess;
     const KernelSet &k = kernels(shape, v);
     const int want = (int)(bytes < 100 * 1024 ? 100 * 1024 : bytes);
-    cudaError_t e = cudaFuncSetAttribute((const void *)k.scan, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)k.drain, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    if (e != cudaSuccess) return e;
-    for (void (*f)(EngineArgs) : {k.reg.scan, k.reg.drain, k.reg.drain_hi, k.coop.scan, k.coop.drain}) {
+    cudaError_t e;
+    for (void (*f)(EngineArgs) : {k.scan, k.drain, k.reg.scan, k.reg.drain, k.reg.drain_hi, k.coop.scan, k.coop.drain}) {
         if (!f) continue;
         e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e != cudaSuccess) return e;
@@ -165,7 +171,7 @@ static int drain_grid(const iwpp_plan &p, int v, uint32_t ntiles) {
     const KernelSet &k = kernels(shape, v);
     if (!has_kernels(p, k)) return 0;
     const size_t smem = drain_smem(p, k);
-    if (ensure_smem_attr(shape, v, k.smem((uint32_t)p.smem_queue_cap)) != cudaSuccess) return 0;
+    if (ensure_smem_attr(shape, v, k.smem ? k.smem((uint32_t)p.smem_queue_cap) : smem) != cudaSuccess) return 0;
     int bps = p.blocks_per_sm;
     if (bps <= 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, drain_fn(p, k), kThreads, smem) != cudaSuccess)
@@ -191,7 +197,7 @@ bool plan_valid(const iwpp_plan &p) {
         return false;
     if (p.local_solver == IWPP_SOLVER_COOP &&
         (!coop_kernel_set(p.tile_h, p.tile_w, 0).drain || p.value_levels > 1 || p.blocks_per_sm > kCoopBlocks ||
-         p.sweeps != 0 || p.revisit_sweeps != 0))
+         p.revisit_sweeps != 0))
         return false;
     if (p.local_solver == IWPP_SOLVER_REGISTER && !reg_kernel_set(p.tile_h, p.tile_w, 0).drain) return false;
     if (p.value_levels < 0 || p.value_levels > kMaxLevels) return false;
@@ -199,28 +205,23 @@ bool plan_valid(const iwpp_plan &p) {
     return true;
 }
 
-// The measured best static plans. Batches: 16 x 64 tiles settled by the register solver
-// (one tile per warp), no sweeps before the persistent kernel (the scan kernel still checks
-// the precondition and collects the frontier). Single images: 64 x 64 tiles settled by the
-// cooperative solver (one tile per CTA of four warps).
-void default_batch_plan(iwpp_plan *p) {
-    p->tile_h = 16;
+// The measured best static plan, for single images and batches alike: 64 x 64 tiles
+// settled by the cooperative solver (one tile per CTA of four warps), no sweeps before the
+// persistent kernel (the scan kernel still checks the precondition and collects the
+// frontier). The autotuner picked it on every batch measured.
+void default_plan(iwpp_plan *p) {
+    p->tile_h = 64;
     p->tile_w = 64;
     p->sweeps = 0;
     p->revisit_sweeps = 0;
     p->smem_queue_cap = 512;
     p->blocks_per_sm = 0;
-    p->local_solver = IWPP_SOLVER_REGISTER;
+    p->local_solver = IWPP_SOLVER_COOP;
     p->value_levels = 0;
     p->watchdog_ns = 0;
 }
 
-void default_plan(iwpp_plan *p) {
-    default_batch_plan(p);
-    p->tile_h = 64;
-    p->tile_w = 64;
-    p->local_solver = IWPP_SOLVER_COOP;
-}
+void default_batch_plan(iwpp_plan *p) { default_plan(p); }
 
 // Pixel offsets are 64-bit everywhere; sides stay below 2^31 (ints in the kernels) and
 // the pixel count below 2^40, which keeps the tile count of any plan below 2^31.
@@ -265,6 +266,7 @@ static void fill_common(EngineArgs &a, const iwpp_plan &p, uint8_t *base, size_t
     a.nimg = 0;
     a.nlevels = p.value_levels > 1 ? (uint32_t)p.value_levels : 1u;
     a.lvl = nullptr;
+    a.tile_img = nullptr;
 }
 
 // ---- single image ------------------------------------------------------------------------------
@@ -294,8 +296,6 @@ static bool make_layout(int64_t H, int64_t W, int v, const iwpp_plan &p, Layout 
     return true;
 }
 
-// Phases of one call: bit 0 = workspace reset + scan kernel, bit 1 = persistent drain.
-enum { kPhaseScan = 1, kPhaseDrain = 2 };
 
 int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int conn, int op, int dtype,
                     const iwpp_plan *plan_in, void *ws, size_t ws_bytes, cudaStream_t stream, int phases) {
@@ -353,10 +353,10 @@ size_t workspace_bytes(int64_t H, int64_t W, int dtype, const iwpp_plan *plan_in
 }
 
 // ---- batch -------------------------------------------------------------------------------------
-// Workspace: header (256 B) | image table | tile states | tile-queue slots | overflow queues.
-// Tiles are numbered image by image, row-major inside an image.
+// Workspace: header (256 B) | image table | tile states | tile-queue slots | tile -> image map |
+// overflow queues. Tiles are numbered image by image, row-major inside an image.
 struct BatchLayout {
-    size_t table, state, queue, ovf, total;
+    size_t table, state, queue, timg, ovf, total;
     uint32_t ntiles, ovcap;
     int grid;
 };
@@ -386,12 +386,18 @@ int64_t batch_tiles(const iwpp_image *imgs, int n, const iwpp_plan &p, std::vect
 }
 
 // Kernel variant of a batch: the specialised one when every image has the same pixel
-// type and connectivity, else the mixed one.
-static int batch_variant(const iwpp_image *imgs, int n) {
+// type and connectivity; under the cooperative solver, the one of the batch's
+// connectivity when only the pixel types differ; else the mixed one.
+static int batch_variant(const iwpp_image *imgs, int n, const iwpp_plan &p) {
     const int v = kind_of(imgs[0].dtype, imgs[0].connectivity);
-    for (int i = 1; i < n; i++)
-        if (kind_of(imgs[i].dtype, imgs[i].connectivity) != v) return kMixed;
-    return v;
+    bool same_kind = true, same_conn = true;
+    for (int i = 1; i < n; i++) {
+        same_kind = same_kind && kind_of(imgs[i].dtype, imgs[i].connectivity) == v;
+        same_conn = same_conn && imgs[i].connectivity == imgs[0].connectivity;
+    }
+    if (same_kind) return v;
+    if (same_conn && p.local_solver == IWPP_SOLVER_COOP) return imgs[0].connectivity == 8 ? kAnyPix8 : kAnyPix4;
+    return kMixed;
 }
 
 static bool make_batch_layout(const iwpp_image *imgs, int n, const iwpp_plan &p, BatchLayout &L,
@@ -399,13 +405,14 @@ static bool make_batch_layout(const iwpp_image *imgs, int n, const iwpp_plan &p,
     const int64_t nt = batch_tiles(imgs, n, p, bases);
     if (nt < 1) return false;
     L.ntiles = (uint32_t)nt;
-    L.grid = drain_grid(p, batch_variant(imgs, n), L.ntiles);
+    L.grid = drain_grid(p, batch_variant(imgs, n, p), L.ntiles);
     if (L.grid <= 0) return false;
     L.ovcap = p.local_solver == IWPP_SOLVER_QUEUE ? (uint32_t)(p.tile_h * p.tile_w - p.smem_queue_cap) : 0u;
     L.table = 256;
     L.state = L.table + align256((size_t)n * sizeof(ImageView));
     L.queue = L.state + align256((size_t)L.ntiles * 4);
-    L.ovf = L.queue + align256((size_t)L.ntiles * 4);
+    L.timg = L.queue + align256((size_t)L.ntiles * 4);
+    L.ovf = L.timg + align256((size_t)L.ntiles * 4);
     L.total = L.ovf + align256((size_t)L.grid * kWarpsPerCta * 2 * L.ovcap * sizeof(uint16_t) + 16);
     return true;
 }
@@ -421,7 +428,8 @@ size_t batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *pla
 
 int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, const uint32_t *order,
                       const uint8_t *tile_sweeps, uint32_t *tile_work, void *ws, size_t ws_bytes,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, int phases) {
+    if (phases < 1 || phases > 3) return IWPP_ERR_ARG;
     iwpp_plan p;
     if (plan_in) p = *plan_in; else default_batch_plan(&p);
     if (!plan_valid(p) || p.value_levels > 1) return IWPP_ERR_ARG;   // batches: one FIFO
@@ -446,13 +454,18 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     a.order = order;
     a.tile_work = tile_work;
     a.defer_push = 1;
+    a.tile_img = reinterpret_cast<const uint32_t *>(base + L.timg);
 
     const int shape = shape_index(p.tile_h, p.tile_w);
-    const int variant = batch_variant(imgs, n);
+    const int variant = batch_variant(imgs, n, p);
     const KernelSet &k = kernels(shape, variant);
-    const size_t smem = k.smem(a.qcap);
+    const size_t smem = k.smem ? k.smem(a.qcap) : drain_smem(p, k);
     if (ensure_smem_attr(shape, variant, smem) != cudaSuccess) return IWPP_ERR_CUDA;
 
+    if ((phases & kPhaseScan) == 0) {   // drain only: the prepared workspace is reused
+        drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
+        return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
+    }
     // image table: descriptors travel as kernel parameters (no host-to-device copy)
     for (int first = 0; first < n; first += kDescChunk) {
         DescChunk c;
@@ -464,6 +477,11 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
         }
         upload_descs_kernel<<<1, kDescChunk, 0, stream>>>(table, c);
     }
+    {
+        const int sms = device_sm_count();
+        const int g = n < sms * 4 ? n : sms * 4;
+        tile_image_kernel<<<g, 256, 0, stream>>>(table, n, reinterpret_cast<uint32_t *>(base + L.timg));
+    }
     if (cudaMemsetAsync(base, 0, 256, stream) != cudaSuccess) return IWPP_ERR_CUDA;
     if (cudaMemsetAsync(base + L.state, 0, (size_t)L.ntiles * 4, stream) != cudaSuccess) return IWPP_ERR_CUDA;
     if (cudaMemsetAsync(base + L.queue, 0xFF, (size_t)L.ntiles * 4, stream) != cudaSuccess) return IWPP_ERR_CUDA;
@@ -474,8 +492,14 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     const uint32_t cgrid = (L.ntiles + 255) / 256 < (uint32_t)(sms * 8) ? (L.ntiles + 255) / 256 : (uint32_t)(sms * 8);
     compact_kernel<<<cgrid, 256, 0, stream>>>(a);
     finalize_queue_kernel<<<cgrid, 256, 0, stream>>>(a);
-    drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
+    if (phases & kPhaseDrain) drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
+}
+
+// Kernel launches one batch call makes (for launch accounting by callers).
+int batch_launches(int n, int phases) {
+    const int prep = (n + kDescChunk - 1) / kDescChunk + 4;   // table chunks, tile map, scan, compact, finalize
+    return ((phases & kPhaseScan) ? prep : 0) + ((phases & kPhaseDrain) ? 1 : 0);
 }
 
 }  // namespace iwpp
@@ -543,7 +567,7 @@ extern "C" size_t iwpp_batch_workspace_bytes(const iwpp_image *imgs, int n, cons
 extern "C" int iwpp_reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan, void *workspace,
                                       size_t ws_bytes, void *stream) {
     return iwpp::reconstruct_batch(imgs, n, plan, nullptr, nullptr, nullptr, workspace, ws_bytes,
-                                   static_cast<cudaStream_t>(stream));
+                                   static_cast<cudaStream_t>(stream), iwpp::kPhaseScan | iwpp::kPhaseDrain);
 }
 
 extern "C" int iwpp_reconstruct_batch_sched(const iwpp_image *imgs, int n, const iwpp_plan *plan,
@@ -551,7 +575,20 @@ extern "C" int iwpp_reconstruct_batch_sched(const iwpp_image *imgs, int n, const
                                             uint32_t *tile_work, void *workspace, size_t ws_bytes,
                                             void *stream) {
     return iwpp::reconstruct_batch(imgs, n, plan, tile_order, tile_sweeps, tile_work, workspace, ws_bytes,
-                                   static_cast<cudaStream_t>(stream));
+                                   static_cast<cudaStream_t>(stream), iwpp::kPhaseScan | iwpp::kPhaseDrain);
+}
+
+extern "C" int iwpp_reconstruct_batch_phase(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                            const uint32_t *tile_order, const uint8_t *tile_sweeps,
+                                            uint32_t *tile_work, int phases, void *workspace, size_t ws_bytes,
+                                            void *stream) {
+    return iwpp::reconstruct_batch(imgs, n, plan, tile_order, tile_sweeps, tile_work, workspace, ws_bytes,
+                                   static_cast<cudaStream_t>(stream), phases);
+}
+
+extern "C" int iwpp_batch_launch_count(int n, int phases) {
+    if (n < 1 || phases < 1 || phases > 3) return -1;
+    return iwpp::batch_launches(n, phases);
 }
 
 extern "C" int iwpp_sync_status(const void *workspace, void *stream) {

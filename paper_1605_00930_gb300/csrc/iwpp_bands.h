@@ -33,6 +33,14 @@ class BandSchedule {
         return -1;
     }
 
+    // The band next() would return after visited(b, true): the best guess of the next visit
+    // while band b is still being reconstructed (a band that changes dirties its neighbours).
+    int64_t peek_after_change(int64_t b) const {
+        BandSchedule t = *this;
+        t.visited(b, true);
+        return t.next();
+    }
+
     // Report the visit of band b: it is clean now; if its rows changed, its neighbours are dirty.
     void visited(int64_t b, bool changed) {
         const int64_t nb = (int64_t)dirty_.size();

@@ -55,11 +55,31 @@ __device__ __forceinline__ void coop_fold_misc(CoopShared &C, const uint32_t *m,
     atomicMax(&C.misc[5], m[5]);
 }
 
+#if IWPP_PHASE_TIMING
+#define IWPP_CO_MARK(k)                                  \
+    do {                                                 \
+        if (w == 0) {                                    \
+            const long long _n = clock64();              \
+            ph[k] += (unsigned long long)(_n - pt);      \
+            pt = _n;                                     \
+        }                                                \
+    } while (0)
+#else
+#define IWPP_CO_MARK(k) \
+    do {                \
+    } while (0)
+#endif
+
 // One visit of CTA tile t by the whole CTA (every thread calls it with the same t), including
 // the re-processing rounds when the tile is notified while the CTA holds it.
 template <typename T, int CONN>
 __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem,
-                                CoopShared &C, VisitStats &st, int w, int lane) {
+                                CoopShared &C, VisitStats &st, unsigned long long *ph, int w, int lane) {
+    (void)ph;
+#if IWPP_PHASE_TIMING
+    long long pt = clock64();
+#endif
+    const long long c0 = clock64();
     constexpr int TH = kCoopStrip;
     using RT = RegTile<T, CONN, TH>;
     const typename RT::Smem s = RT::carve(wsmem);
@@ -69,51 +89,73 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
     const int y0 = ty * kCoopRows + TH * w, x0 = tx * RT::TW;
     if (lane < 16) s.misc[lane] = 0;
     if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
+    IWPP_CO_MARK(6);
     uint32_t J[TH], I[TH], jt, jb, it, ib;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+    IWPP_CO_MARK(0);
     uint32_t passes = 0;
+    // settled: the strip is a fixed point of J <- min(I, max over the neighbourhood) for
+    // its current halo
+    bool settled = false;
     for (;;) {
         uint32_t rows = 0;
-        bool active = true;
+        bool up_fresh = false;   // the strip's last pass was an up pass run with its current halo
         for (;;) {   // joint iterations of the strips
-            uint32_t ch = 0;
-            if (active) {
-                ch = RT::pass_down(hx, J, I, jt, lane);
-                ch |= RT::pass_up(hx, J, I, jb, lane);
-                passes += 2;
-                rows |= ch;
+            if (!settled) {
+                const uint32_t chd = RT::pass_down(hx, J, I, jt, lane);
+                passes++;
+                rows |= chd;
+                // A down pass that changes nothing right after an up pass with the same halo
+                // leaves every pixel checked, with final values, against its neighbours below
+                // (by the up pass) and above and beside it (by the down pass): settled.
+                if (up_fresh && !__any_sync(0xffffffffu, chd != 0)) {
+                    settled = true;
+                } else {
+                    const uint32_t chu = RT::pass_up(hx, J, I, jb, lane);
+                    passes++;
+                    rows |= chu;
+                    // likewise an up pass that changes nothing after a down pass with the same
+                    // halo (a strip that changed may still be short of its fixed point: its
+                    // next pass finds out, measured cheaper than a residual check here)
+                    settled = !__any_sync(0xffffffffu, chu != 0);
+                    up_fresh = true;
+                }
             }
             C.rows[w][0][lane] = J[0];
             C.rows[w][1][lane] = J[TH - 1];
             __syncthreads();
             const uint32_t njt = w > 0 ? C.rows[w - 1][1][lane] : jt;
             const uint32_t njb = w < kWarpsPerCta - 1 ? C.rows[w + 1][0][lane] : jb;
-            const bool halo = __any_sync(0xffffffffu, njt != jt || njb != jb);
+            const bool tchg = __any_sync(0xffffffffu, njt != jt), bchg = __any_sync(0xffffffffu, njb != jb);
+            if (tchg || bchg) {   // a neighbour strip's boundary row changed: new work possible
+                up_fresh = false;
+                settled = false;
+            }
             jt = njt;
             jb = njb;
-            // a strip that changed may still be short of its fixed point (its next pass pair
-            // finds out: measured cheaper than a residual check here); one whose halo rows
-            // changed may have new work; the others are settled
-            active = halo || __any_sync(0xffffffffu, ch != 0);
-            if (!__syncthreads_or(active)) break;
+            if (!__syncthreads_or(!settled)) break;
         }
         if (w == 0 && lane == 0) st.visits++;
+        IWPP_CO_MARK(1);
         if (__syncthreads_or(rows != 0)) {
             RT::store(im, y0, x0, J, rows, lane);
             RT::notify_scan(s, J, jt, jb, it, ib, lane);
             if (lane == 0) coop_fold_misc(C, s.misc, w);
-            __threadfence();
+            fence_protocol();
             __syncthreads();
+            IWPP_CO_MARK(2);
             if (w == 0 && lane < 9 && lane != 4 && C.misc[lane]) {
                 const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
                 if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x)
                     notify_tile(a, im.tile_base + (uint32_t)(ny * im.tiles_x + nx));
             }
+            IWPP_CO_MARK(3);
         }
         if (w == 0) {
             const bool r = finish_tile(a, t, lane);
             if (lane == 0) C.redo = r;
         }
+        IWPP_CO_MARK(4);
         __syncthreads();
         const bool redo = C.redo != 0;
         if (!redo) break;
@@ -122,24 +164,36 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
         if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
         RT::load_halo(im, s, y0, x0, jt, jb, it, ib, false, lane);
         __syncthreads();
+        settled = false;
+        IWPP_CO_MARK(5);
     }
     st.waves += passes;
+    if (w == 0 && lane == 0 && a.tile_work) {   // per-tile work: warp 0's passes, the visit's SM cycles
+        atomicAdd(a.tile_work + t, passes);
+        atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
+    }
 }
 
 // One CTA tile visit, dispatched on the tile's image kind (CTA-uniform: one tile per CTA).
 template <typename T, int CONN, bool MIXED>
 __device__ __forceinline__ void visit_tile_coop_any(const EngineArgs &a, uint32_t t, uint8_t *wsmem, CoopShared &C,
-                                                    VisitStats &st, int w, int lane) {
+                                                    VisitStats &st, unsigned long long *ph, int w, int lane) {
+#if IWPP_PHASE_TIMING
+    const long long c0 = clock64();
+#endif
     const ImageView &im = image_of(a, t);
+#if IWPP_PHASE_TIMING
+    if (w == 0) ph[7] += (unsigned long long)(clock64() - c0);
+#endif
     if (!MIXED) {
-        visit_tile_coop<T, CONN>(a, im, t, wsmem, C, st, w, lane);
+        visit_tile_coop<T, CONN>(a, im, t, wsmem, C, st, ph, w, lane);
         return;
     }
     switch (im.kind) {
-        case 0: visit_tile_coop<uint8_t, 4>(a, im, t, wsmem, C, st, w, lane); break;
-        case 1: visit_tile_coop<uint16_t, 4>(a, im, t, wsmem, C, st, w, lane); break;
-        case 2: visit_tile_coop<uint8_t, 8>(a, im, t, wsmem, C, st, w, lane); break;
-        default: visit_tile_coop<uint16_t, 8>(a, im, t, wsmem, C, st, w, lane); break;
+        case 0: visit_tile_coop<uint8_t, 4>(a, im, t, wsmem, C, st, ph, w, lane); break;
+        case 1: visit_tile_coop<uint16_t, 4>(a, im, t, wsmem, C, st, ph, w, lane); break;
+        case 2: visit_tile_coop<uint8_t, 8>(a, im, t, wsmem, C, st, ph, w, lane); break;
+        default: visit_tile_coop<uint16_t, 8>(a, im, t, wsmem, C, st, ph, w, lane); break;
     }
 }
 
@@ -155,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, MIXED ? kRegBlocks : kCoopBlocks) dr
     uint8_t *wsmem = smem_raw + warp * RT::smem_per_warp(0);
     CoopShared &C = *reinterpret_cast<CoopShared *>(smem_raw + kWarpsPerCta * RT::smem_per_warp(0));
     VisitStats st = {0, 0, 0, 0};
-    unsigned long long idle = 0, busy = 0;
+    unsigned long long idle = 0, busy = 0, ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (;;) {
         if (warp == 0) {
             bool first;
@@ -166,20 +220,28 @@ __global__ void __launch_bounds__(kThreads, MIXED ? kRegBlocks : kCoopBlocks) dr
         const uint32_t t = C.tile;
         if (t == kDone) break;
         const unsigned long long b0 = globaltimer_ns();
-        visit_tile_coop_any<T, CONN, MIXED>(a, t, wsmem, C, st, warp, lane);
+        visit_tile_coop_any<T, CONN, MIXED>(a, t, wsmem, C, st, ph, warp, lane);
         if (warp == 0) busy += globaltimer_ns() - b0;
         __syncthreads();   // every warp has read C.tile before the next pop overwrites it
     }
-    flush_stats(a, st, idle, busy, lane);
+    flush_stats(a, st, idle, busy, lane);   // passes of every strip; visits and times of warp 0
+#if IWPP_PHASE_TIMING
+    if (warp == 0 && lane == 0)
+        for (int k = 0; k < 8; k++) atomicAdd(&a.hdr->phase_cycles[k], ph[k]);
+#endif
 }
 
-// Initial frontier of one CTA tile: queue it if one of its pixels can rise (each strip checks
-// its own pixels against its neighbourhood, halo included), and check the precondition.
+// Initialisation of one CTA tile (Algorithm 7's scanning phase, tile-local, then the
+// frontier): check the precondition; run the tile's raster / anti-raster sweep pairs
+// (a.tile_sweeps[t], else a.sweeps), the strips exchanging their boundary rows after each
+// pair, store what changed and notify the neighbours whose halo pixels the tile can now
+// raise; queue the tile if one of its pixels can still rise.
 template <typename T, int CONN>
-__device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem, int w,
-                               int lane) {
+__device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem,
+                               CoopShared &C, int w, int lane) {
     constexpr int TH = kCoopStrip;
     using RT = RegTile<T, CONN, TH>;
+    const long long c0 = clock64();
     const typename RT::Smem s = RT::carve(wsmem);
     const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
     const uint32_t lt = t - im.tile_base;
@@ -190,14 +252,43 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
+    const int sweeps = a.tile_sweeps ? (int)a.tile_sweeps[t] : a.sweeps;   // CTA-uniform
+    uint32_t rows = 0;
+    for (int k = 0; k < sweeps; k++) {
+        rows |= RT::sweep_raster(hx, J, I, jt, lane);
+        rows |= RT::sweep_antiraster(hx, J, I, jb, lane);
+        C.rows[w][0][lane] = J[0];
+        C.rows[w][1][lane] = J[TH - 1];
+        __syncthreads();
+        if (w > 0) jt = C.rows[w - 1][1][lane];
+        if (w < kWarpsPerCta - 1) jb = C.rows[w + 1][0][lane];
+        __syncthreads();
+    }
     const bool can = RT::improvable(hx, J, I, jt, jb, lane);
     const int any_bad = __syncthreads_or(bad);
     const int any_can = __syncthreads_or(can);
+    if (sweeps > 0 && __syncthreads_or(rows != 0)) {
+        RT::store(im, y0, x0, J, rows, lane);
+        if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
+        __syncthreads();
+        RT::notify_scan(s, J, jt, jb, it, ib, lane);
+        if (lane == 0) coop_fold_misc(C, s.misc, w);
+        fence_protocol();
+        __syncthreads();
+        if (w == 0 && lane < 9 && lane != 4 && C.misc[lane]) {
+            const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+            if (ny >= 0 && nx >= 0 && ny < im.tiles_y && nx < im.tiles_x) {
+                const uint32_t n = im.tile_base + (uint32_t)(ny * im.tiles_x + nx);
+                if (a.defer_push) mark_pending(a, n); else notify_tile(a, n);
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         if (any_can) {
             if (a.defer_push) mark_pending(a, t); else notify_tile(a, t);   // batches: queued in order later
         }
         if (any_bad) set_status(a.hdr, kErrPrecondition);
+        if (a.tile_work) atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
     }
     __syncthreads();   // the strips' shared halo buffers are reloaded for the next tile
 }
@@ -208,17 +299,18 @@ __global__ void __launch_bounds__(kThreads) scan_coop_kernel(EngineArgs a) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *wsmem = smem_raw + w * RT::smem_per_warp(0);
+    CoopShared &C = *reinterpret_cast<CoopShared *>(smem_raw + kWarpsPerCta * RT::smem_per_warp(0));
     for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const ImageView &im = image_of(a, t);
         if (!MIXED) {
-            scan_tile_coop<T, CONN>(a, im, t, wsmem, w, lane);
+            scan_tile_coop<T, CONN>(a, im, t, wsmem, C, w, lane);
             continue;
         }
         switch (im.kind) {
-            case 0: scan_tile_coop<uint8_t, 4>(a, im, t, wsmem, w, lane); break;
-            case 1: scan_tile_coop<uint16_t, 4>(a, im, t, wsmem, w, lane); break;
-            case 2: scan_tile_coop<uint8_t, 8>(a, im, t, wsmem, w, lane); break;
-            default: scan_tile_coop<uint16_t, 8>(a, im, t, wsmem, w, lane); break;
+            case 0: scan_tile_coop<uint8_t, 4>(a, im, t, wsmem, C, w, lane); break;
+            case 1: scan_tile_coop<uint16_t, 4>(a, im, t, wsmem, C, w, lane); break;
+            case 2: scan_tile_coop<uint8_t, 8>(a, im, t, wsmem, C, w, lane); break;
+            default: scan_tile_coop<uint16_t, 8>(a, im, t, wsmem, C, w, lane); break;
         }
     }
 }

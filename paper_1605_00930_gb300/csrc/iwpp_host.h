@@ -22,7 +22,10 @@ struct RegKernelSet {
     size_t (*smem)(uint32_t);
 };
 constexpr int kRegBlocks = 4, kRegHiBlocks = 6;
-constexpr int kCoopBlocks = 5;   // CTAs per SM of the cooperative solver's persistent kernel
+#ifndef IWPP_COOP_MINB
+#define IWPP_COOP_MINB 5
+#endif
+constexpr int kCoopBlocks = IWPP_COOP_MINB;   // CTAs per SM of the cooperative solver's persistent kernel
 RegKernelSet reg_kernel_set(int th, int tw, int v);
 RegKernelSet coop_kernel_set(int th, int tw, int v);   // cooperative solver (64 x 64 tiles)
 
@@ -37,7 +40,11 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
 size_t workspace_bytes(int64_t H, int64_t W, int dtype, const iwpp_plan *plan);
 int64_t batch_tiles(const iwpp_image *imgs, int n, const iwpp_plan &p, std::vector<uint32_t> *bases);
 size_t batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan);
+// Phases of a call: bit 0 = workspace reset + scan (batches: table upload, scan, queue
+// compaction), bit 1 = persistent drain.
+enum { kPhaseScan = 1, kPhaseDrain = 2 };
 int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan, const uint32_t *order,
                       const uint8_t *tile_sweeps, uint32_t *tile_work, void *ws, size_t ws_bytes,
-                      cudaStream_t stream);
+                      cudaStream_t stream, int phases);
+int batch_launches(int n, int phases);
 }  // namespace iwpp

@@ -24,6 +24,8 @@ RegKernelSet coop_kernel_set(int th, int tw, int v) {
         case 2: return coop_set<uint8_t, 8>();
         case 3: return coop_set<uint16_t, 8>();
         case 4: return coop_set<uint16_t, 8, true>();   // mixed batches
+        case 5: return coop_set<AnyPix, 4>();           // u8 and u16 images, 4-connectivity
+        case 6: return coop_set<AnyPix, 8>();           // u8 and u16 images, 8-connectivity
         default: return none;
     }
 }

@@ -49,13 +49,22 @@ int scratch_address(void **out) {
 extern "C" int iwpp_reconstruct_noalloc(void *marker_inout, const void *mask, int64_t H, int64_t W,
                                         int connectivity, int op, int dtype, void *stream, int *status_out) {
     if (!marker_inout || !mask) return IWPP_ERR_ARG;
-    const size_t need = iwpp::workspace_bytes(H, W, dtype, nullptr);   // default plan; 0 = bad size or dtype
-    if (need == 0) return IWPP_ERR_ARG;
+    if (H < 1 || W < 1 || H >= (1ll << 31) || W >= (1ll << 31) || (uint64_t)H * (uint64_t)W >= (1ull << 40))
+        return IWPP_ERR_ARG;
+    if (dtype != IWPP_U8 && dtype != IWPP_U16) return IWPP_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (status_out != nullptr) {   // waiting for the status would break a capture of `stream`
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return IWPP_ERR_CUDA;
+        if (cs != cudaStreamCaptureStatusNone) return IWPP_ERR_ARG;
+    }
+    // default plan; with valid sizes and dtype a zero here means a CUDA query failed
+    const size_t need = iwpp::workspace_bytes(H, W, dtype, nullptr);
+    if (need == 0) return IWPP_ERR_CUDA;
     if (need > kScratchBytes) return IWPP_ERR_WORKSPACE;               // image too large for the scratch
     void *ws = nullptr;
     const int rc = scratch_address(&ws);
     if (rc != IWPP_OK) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     // The call resets the parts of the scratch that must start at zero (header, tile states)
     // and the tile queue itself, on `stream`, before its kernels run.
     const int r = iwpp::reconstruct_one(marker_inout, mask, H, W, connectivity, op, dtype, nullptr, ws,

@@ -35,8 +35,11 @@ __global__ void band_done_kernel(const T *before, const T *after, size_t n, cons
     if (blockIdx.x == 0 && threadIdx.x == 0 && *band_status != 0) atomicCAS(acc, 0u, *band_status);
 }
 
+// Workspace: flags (256 B) | two band buffers, each: marker plane and mask plane of
+// (band_rows + 2) x W (band plus halo rows) and a band_rows x W copy of the band from before
+// its reconstruction | a single-image workspace for band_rows + 2 rows.
 struct OocLayout {
-    size_t acc, jb, ib, j0, rws, total;
+    size_t acc, buf[2], plane, jcopy, rws, total;
     size_t rws_bytes;
     int64_t band;
 };
@@ -48,17 +51,37 @@ bool ooc_layout(int64_t H, int64_t W, int dtype, int64_t band_rows, OocLayout &L
     const int64_t rows = L.band + 2;
     if ((uint64_t)rows * (uint64_t)W >= (1ull << 40)) return false;
     const size_t s = dtype == IWPP_U16 ? 2 : 1;
-    const size_t plane = (size_t)rows * (size_t)W * s;
+    L.plane = align256((size_t)rows * (size_t)W * s);
+    L.jcopy = align256((size_t)L.band * (size_t)W * s);
     L.rws_bytes = workspace_bytes(rows, W, dtype, nullptr);
     if (L.rws_bytes == 0) return false;
     L.acc = 0;
-    L.jb = 256;
-    L.ib = L.jb + align256(plane);
-    L.j0 = L.ib + align256(plane);
-    L.rws = L.j0 + align256((size_t)L.band * (size_t)W * s);
+    L.buf[0] = 256;
+    L.buf[1] = L.buf[0] + 2 * L.plane + L.jcopy;
+    L.rws = L.buf[1] + 2 * L.plane + L.jcopy;
     L.total = L.rws + align256(L.rws_bytes);
     return true;
 }
+
+// One device band buffer and the band it holds.
+struct BandBuf {
+    uint8_t *jb, *ib, *j0;
+    int64_t band = -1;
+    cudaEvent_t loaded = nullptr, free = nullptr;
+};
+
+// CUDA objects of one call, released on every return path.
+struct OocRes {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t *flags = nullptr;   // pinned host [0] first error, [1] changed
+    ~OocRes() {
+        if (copy) cudaStreamDestroy(copy);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (flags) cudaFreeHost(flags);
+    }
+};
 
 }  // namespace
 }  // namespace iwpp
@@ -82,31 +105,83 @@ extern "C" int iwpp_reconstruct_host(void *marker_inout, const void *mask, int64
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t *base = static_cast<uint8_t *>(workspace);
     uint32_t *acc = reinterpret_cast<uint32_t *>(base + L.acc);   // [0] first error, [1] changed
-    uint8_t *jb = base + L.jb, *ib = base + L.ib, *j0 = base + L.j0, *rws = base + L.rws;
+    uint8_t *rws = base + L.rws;
     uint8_t *hm = static_cast<uint8_t *>(marker_inout);
     const uint8_t *hi = static_cast<const uint8_t *>(mask);
     const size_t es = dtype == IWPP_U16 ? 2 : 1, rowb = (size_t)W * es;
     const int64_t nb = (H + L.band - 1) / L.band;
     const int sms = device_sm_count();
     if (sms <= 0) return IWPP_ERR_CUDA;
+
+    // Copies of the next band run on a stream of their own while the current band is
+    // reconstructed on `stream`; events order the two.
+    OocRes R;
+    if (cudaStreamCreateWithFlags(&R.copy, cudaStreamNonBlocking) != cudaSuccess) return IWPP_ERR_CUDA;
+    for (cudaEvent_t &e : R.ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return IWPP_ERR_CUDA;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&R.flags), 8, cudaHostAllocDefault) != cudaSuccess) return IWPP_ERR_CUDA;
+    BandBuf buf[2];
+    for (int k = 0; k < 2; k++) {
+        buf[k].jb = base + L.buf[k];
+        buf[k].ib = buf[k].jb + L.plane;
+        buf[k].j0 = buf[k].ib + L.plane;
+        buf[k].loaded = R.ev[k];
+        buf[k].free = R.ev[2 + k];
+        if (cudaEventRecord(buf[k].free, s) != cudaSuccess) return IWPP_ERR_CUDA;
+    }
+    cudaEvent_t done = R.ev[4];
     if (cudaMemsetAsync(acc, 0, 8, s) != cudaSuccess) return IWPP_ERR_CUDA;
 
-    auto do_band = [&](int64_t b) -> int {
-        const int64_t y0 = b * L.band, y1 = y0 + L.band < H ? y0 + L.band : H;
-        const int64_t top = y0 > 0 ? 1 : 0, bot = y1 < H ? 1 : 0;
+    auto geometry = [&](int64_t b, int64_t &y0, int64_t &y1, int64_t &top, int64_t &bot) {
+        y0 = b * L.band;
+        y1 = y0 + L.band < H ? y0 + L.band : H;
+        top = y0 > 0 ? 1 : 0;
+        bot = y1 < H ? 1 : 0;
+    };
+    // Copy band b (with its halo rows) from host memory into buffer B, on the copy stream,
+    // once B's previous band is done with it.
+    auto upload = [&](BandBuf &B, int64_t b) -> int {
+        int64_t y0, y1, top, bot;
+        geometry(b, y0, y1, top, bot);
         const int64_t r0 = y0 - top, rows = (y1 - y0) + top + bot;
-        const size_t nbytes = (size_t)rows * rowb, band_bytes = (size_t)(y1 - y0) * rowb;
-        if (cudaMemcpyAsync(jb, hm + (size_t)r0 * rowb, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(ib, hi + (size_t)r0 * rowb, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        const size_t nbytes = (size_t)rows * rowb;
+        if (cudaStreamWaitEvent(R.copy, B.free, 0) != cudaSuccess) return IWPP_ERR_CUDA;
+        if (cudaMemcpyAsync(B.jb, hm + (size_t)r0 * rowb, nbytes, cudaMemcpyHostToDevice, R.copy) != cudaSuccess ||
+            cudaMemcpyAsync(B.ib, hi + (size_t)r0 * rowb, nbytes, cudaMemcpyHostToDevice, R.copy) != cudaSuccess)
             return IWPP_ERR_CUDA;
+        if (cudaEventRecord(B.loaded, R.copy) != cudaSuccess) return IWPP_ERR_CUDA;
+        B.band = b;
+        return IWPP_OK;
+    };
+    // Reconstruct the band in B on `stream`. P holds the band visited just before (pb); when
+    // pb is a neighbour, B's halo row on that side may have been copied from host memory
+    // before pb's result reached it, so it is taken from P instead.
+    auto compute = [&](BandBuf &B, BandBuf &P, int64_t pb) -> int {
+        const int64_t b = B.band;
+        int64_t y0, y1, top, bot;
+        geometry(b, y0, y1, top, bot);
+        const int64_t rows = (y1 - y0) + top + bot;
+        const size_t band_bytes = (size_t)(y1 - y0) * rowb;
+        if (cudaStreamWaitEvent(s, B.loaded, 0) != cudaSuccess) return IWPP_ERR_CUDA;
+        if (pb >= 0 && P.band == pb && (pb == b - 1 || pb == b + 1)) {
+            int64_t py0, py1, ptop, pbot;
+            geometry(pb, py0, py1, ptop, pbot);
+            const size_t src = pb == b - 1 ? (size_t)(ptop + (py1 - py0) - 1) * rowb   // P's last band row
+                                           : (size_t)ptop * rowb;                      // P's first band row
+            const size_t dst = pb == b - 1 ? 0 : (size_t)(rows - 1) * rowb;
+            if (cudaMemcpyAsync(B.jb + dst, P.jb + src, rowb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return IWPP_ERR_CUDA;
+            if (cudaEventRecord(P.free, s) != cudaSuccess) return IWPP_ERR_CUDA;   // P is read up to here
+        }
         // halo rows: mask := marker, so they feed the band and cannot change
-        if (top && cudaMemcpyAsync(ib, jb, rowb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return IWPP_ERR_CUDA;
-        if (bot && cudaMemcpyAsync(ib + (size_t)(rows - 1) * rowb, jb + (size_t)(rows - 1) * rowb, rowb,
+        if (top && cudaMemcpyAsync(B.ib, B.jb, rowb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return IWPP_ERR_CUDA;
+        if (bot && cudaMemcpyAsync(B.ib + (size_t)(rows - 1) * rowb, B.jb + (size_t)(rows - 1) * rowb, rowb,
                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return IWPP_ERR_CUDA;
-        if (cudaMemcpyAsync(j0, jb + (size_t)top * rowb, band_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        if (cudaMemcpyAsync(B.j0, B.jb + (size_t)top * rowb, band_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return IWPP_ERR_CUDA;
-        const int rc = reconstruct_one(jb, ib, rows, W, connectivity, op, dtype, nullptr, rws, L.rws_bytes, s, 3);
+        if (cudaMemsetAsync(acc + 1, 0, 4, s) != cudaSuccess) return IWPP_ERR_CUDA;
+        const int rc = reconstruct_one(B.jb, B.ib, rows, W, connectivity, op, dtype, nullptr, rws, L.rws_bytes, s, 3);
         if (rc != IWPP_OK) return rc;
         const size_t n = (size_t)(y1 - y0) * (size_t)W;
         size_t g = (n + 255) / 256;
@@ -114,36 +189,59 @@ extern "C" int iwpp_reconstruct_host(void *marker_inout, const void *mask, int64
         if (g < 1) g = 1;
         const uint32_t *st = reinterpret_cast<const uint32_t *>(rws);
         if (dtype == IWPP_U8)
-            band_done_kernel<uint8_t><<<(unsigned)g, 256, 0, s>>>(j0, jb + (size_t)top * rowb, n, st, acc);
+            band_done_kernel<uint8_t><<<(unsigned)g, 256, 0, s>>>(B.j0, B.jb + (size_t)top * rowb, n, st, acc);
         else
-            band_done_kernel<uint16_t><<<(unsigned)g, 256, 0, s>>>(reinterpret_cast<const uint16_t *>(j0),
-                                                                   reinterpret_cast<const uint16_t *>(jb + top * rowb),
+            band_done_kernel<uint16_t><<<(unsigned)g, 256, 0, s>>>(reinterpret_cast<const uint16_t *>(B.j0),
+                                                                   reinterpret_cast<const uint16_t *>(B.jb + top * rowb),
                                                                    n, st, acc);
         if (cudaGetLastError() != cudaSuccess) return IWPP_ERR_CUDA;
-        if (cudaMemcpyAsync(hm + (size_t)y0 * rowb, jb + (size_t)top * rowb, band_bytes, cudaMemcpyDeviceToHost,
+        if (cudaMemcpyAsync(R.flags, acc, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(hm + (size_t)y0 * rowb, B.jb + (size_t)top * rowb, band_bytes, cudaMemcpyDeviceToHost,
                             s) != cudaSuccess)
             return IWPP_ERR_CUDA;
+        if (cudaEventRecord(B.free, s) != cudaSuccess || cudaEventRecord(done, s) != cudaSuccess) return IWPP_ERR_CUDA;
         return IWPP_OK;
     };
 
     // A band is a fixed point given its halo rows once reconstructed; it needs another visit
-    // only when a neighbour band changed afterwards (iwpp_bands.h).
+    // only when a neighbour band changed afterwards (iwpp_bands.h). While a band is
+    // reconstructed, the band expected next (the next one in sweep order if this one changes)
+    // is copied into the other buffer; a wrong guess costs one more copy, never a result.
     BandSchedule order(nb);
     int32_t visits = 0;
-    for (int64_t b = order.next(); b >= 0; b = order.next()) {
-        if (cudaMemsetAsync(acc + 1, 0, 4, s) != cudaSuccess) return IWPP_ERR_CUDA;
-        const int rc = do_band(b);
+    int64_t cur = order.next(), prev = -1;
+    int k = 0;
+    if (cur >= 0) {
+        const int rc = upload(buf[0], cur);
         if (rc != IWPP_OK) return rc;
-        uint32_t h[2] = {0, 0};
-        if (cudaMemcpyAsync(h, acc, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return IWPP_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return IWPP_ERR_CUDA;
-        visits++;
-        if (h[0] != 0) {
-            if (visits_out) *visits_out = visits;
-            return (int)h[0];
-        }
-        order.visited(b, h[1] != 0);
     }
+    while (cur >= 0) {
+        BandBuf &B = buf[k & 1], &O = buf[(k + 1) & 1];
+        int rc = compute(B, O, prev);
+        if (rc != IWPP_OK) return rc;
+        const int64_t guess = order.peek_after_change(cur);
+        if (guess >= 0) {
+            rc = upload(O, guess);
+            if (rc != IWPP_OK) return rc;
+        }
+        if (cudaEventSynchronize(done) != cudaSuccess) return IWPP_ERR_CUDA;
+        visits++;
+        if (R.flags[0] != 0) {
+            if (cudaStreamSynchronize(R.copy) != cudaSuccess) return IWPP_ERR_CUDA;
+            if (visits_out) *visits_out = visits;
+            return (int)R.flags[0];
+        }
+        order.visited(cur, R.flags[1] != 0);
+        const int64_t nxt = order.next();
+        if (nxt >= 0 && nxt != guess) {   // wrong guess: copy the band that is due
+            rc = upload(O, nxt);
+            if (rc != IWPP_OK) return rc;
+        }
+        prev = cur;
+        cur = nxt;
+        k++;
+    }
+    if (cudaStreamSynchronize(R.copy) != cudaSuccess) return IWPP_ERR_CUDA;
     if (visits_out) *visits_out = visits;
     return IWPP_OK;
 }

@@ -32,7 +32,7 @@ static int graph_create(const iwpp_image *imgs, int n, const iwpp_plan *plan, co
         cudaStreamDestroy(s);
         return IWPP_ERR_CUDA;
     }
-    const int rc = reconstruct_batch(imgs, n, plan, order, sweeps, nullptr, ws, ws_bytes, s);
+    const int rc = reconstruct_batch(imgs, n, plan, order, sweeps, nullptr, ws, ws_bytes, s, kPhaseScan | kPhaseDrain);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s, &g);
     cudaStreamDestroy(s);
@@ -110,7 +110,9 @@ struct Tuner {
             if (restore() != IWPP_OK) break;
             if (cudaMemsetAsync(flush, r & 0xFF, flush_bytes, stream) != cudaSuccess) break;
             cudaEventRecord(e0, stream);
-            if (reconstruct_batch(imgs, n, &p, nullptr, nullptr, nullptr, ws, ws_bytes, stream) != IWPP_OK) break;
+            if (reconstruct_batch(imgs, n, &p, nullptr, nullptr, nullptr, ws, ws_bytes, stream, kPhaseScan | kPhaseDrain) !=
+                IWPP_OK)
+                break;
             cudaEventRecord(e1, stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) break;
             uint32_t st = 1;

@@ -79,6 +79,10 @@ _PROTOS = [
     ("iwpp_reconstruct_batch_sched", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_reconstruct_batch_phase", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_batch_launch_count", ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     ("iwpp_batch_graph_create", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
@@ -171,7 +175,7 @@ def iwpp_default_plan() -> Plan:
 
 
 def iwpp_default_batch_plan() -> Plan:
-    """Default plan of batch calls (16 x 64 tiles, register solver)."""
+    """Default plan of batch calls (the single-image default: 64 x 64 tiles, cooperative solver)."""
     p = Plan()
     lib().iwpp_default_batch_plan(ctypes.byref(p))
     return p
@@ -229,6 +233,16 @@ def iwpp_reconstruct_batch(imgs, plan, ws_ptr, ws_bytes, stream) -> int:
 def iwpp_reconstruct_batch_sched(imgs, plan, order_ptr, sweeps_ptr, work_ptr, ws_ptr, ws_bytes, stream) -> int:
     return lib().iwpp_reconstruct_batch_sched(imgs, len(imgs), _pp(plan), order_ptr, sweeps_ptr, work_ptr,
                                               ws_ptr, ws_bytes, stream)
+
+
+def iwpp_reconstruct_batch_phase(imgs, plan, order_ptr, sweeps_ptr, work_ptr, phases, ws_ptr, ws_bytes,
+                                 stream) -> int:
+    return lib().iwpp_reconstruct_batch_phase(imgs, len(imgs), _pp(plan), order_ptr, sweeps_ptr, work_ptr,
+                                              int(phases), ws_ptr, ws_bytes, stream)
+
+
+def iwpp_batch_launch_count(n: int, phases: int = 3) -> int:
+    return lib().iwpp_batch_launch_count(int(n), int(phases))
 
 
 def iwpp_batch_graph_create(imgs, plan, order_ptr, sweeps_ptr, ws_ptr, ws_bytes):
@@ -629,6 +643,14 @@ class Batch:
             return iwpp_reconstruct_batch(self.descs, self.plan, ws, self.ws.numel(), _stream_handle(stream))
         return iwpp_reconstruct_batch_sched(self.descs, self.plan, _ptr(order), _ptr(sweeps), _ptr(work), ws,
                                             self.ws.numel(), _stream_handle(stream))
+
+    def phase(self, which: str, order=None, sweeps=None, work=None, stream=None) -> int:
+        """Enqueue one step of the batch call: which = "scan" (table upload, reset, scan,
+        queue compaction) or "drain" (the persistent kernel)."""
+        phases = {"scan": 1, "drain": 2, "all": 3}[which]
+        return iwpp_reconstruct_batch_phase(self.descs, self.plan, _ptr(order), _ptr(sweeps), _ptr(work), phases,
+                                            ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                            _stream_handle(stream))
 
     def status(self, stream=None) -> int:
         return iwpp_sync_status(ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream))

@@ -149,22 +149,32 @@ def porous_skiz_case(H: int = 4096, W: int = 4096, nmarkers: int = 2000, nlabels
     return markers, mask
 
 
-def mixed_batch(n: int = 256, workload_id: int = 4, min_side: int = 256, max_side: int = 4096,
-                conn: int = 8) -> list[Case]:
-    """Uneven batch: log-uniform sides, u8/u16 with p = 1/2; the first half are
-    h-dome dilations (h ~ U{10..60}, x257 for u16), the second half fill-holes."""
-    out = []
+def _batch_image(args) -> Case:
+    """Image i of an uneven batch (its own seeded generator, so images are independent)."""
+    i, n, workload_id, min_side, max_side, conn = args
     lo, hi = math.log(min_side), math.log(max_side)
-    for i in range(n):
-        rng = rng_for(workload_id, i)
-        H = int(round(math.exp(rng.uniform(lo, hi))))
-        W = int(round(math.exp(rng.uniform(lo, hi))))
-        is16 = bool(rng.integers(0, 2))
-        field = blob_field_u8(H, W, blob_count(H, W), rng)
-        mask = to_u16(field) if is16 else field
-        if i < n // 2:
-            h = int(rng.integers(10, 61)) * (257 if is16 else 1)
-            out.append(Case(hdome_marker(mask, h), mask, conn, "dilate"))
-        else:
-            out.append(Case(fillholes_marker(mask), mask, conn, "erode"))
-    return out
+    rng = rng_for(workload_id, i)
+    H = int(round(math.exp(rng.uniform(lo, hi))))
+    W = int(round(math.exp(rng.uniform(lo, hi))))
+    is16 = bool(rng.integers(0, 2))
+    field = blob_field_u8(H, W, blob_count(H, W), rng)
+    mask = to_u16(field) if is16 else field
+    if i < n // 2:
+        h = int(rng.integers(10, 61)) * (257 if is16 else 1)
+        return Case(hdome_marker(mask, h), mask, conn, "dilate")
+    return Case(fillholes_marker(mask), mask, conn, "erode")
+
+
+def mixed_batch(n: int = 256, workload_id: int = 4, min_side: int = 256, max_side: int = 4096,
+                conn: int = 8, workers: int = 0) -> list[Case]:
+    """Uneven batch: log-uniform sides, u8/u16 with p = 1/2; the first half are
+    h-dome dilations (h ~ U{10..60}, x257 for u16), the second half fill-holes.
+    workers > 1 generates the images in that many spawned processes (same images)."""
+    jobs = [(i, n, workload_id, min_side, max_side, conn) for i in range(n)]
+    if workers and workers > 1 and n > 1:
+        import multiprocessing
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=min(workers, n),
+                                 mp_context=multiprocessing.get_context("spawn")) as ex:
+            return list(ex.map(_batch_image, jobs, chunksize=max(1, n // (4 * workers))))
+    return [_batch_image(j) for j in jobs]

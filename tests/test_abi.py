@@ -73,7 +73,7 @@ def test_default_plan_and_shapes(iwpp):
     assert p.sweeps >= 0 and 16 <= p.smem_queue_cap <= p.tile_h * p.tile_w
     assert (p.tile_h, p.tile_w, p.local_solver) == (64, 64, iwpp.IWPP_SOLVER_COOP)
     b = iwpp.iwpp_default_batch_plan()
-    assert (b.tile_h, b.tile_w, b.local_solver) == (16, 64, iwpp.IWPP_SOLVER_REGISTER)
+    assert (b.tile_h, b.tile_w, b.local_solver) == (64, 64, iwpp.IWPP_SOLVER_COOP)
     assert iwpp.iwpp_tile_shape_supported(b.tile_h, b.tile_w)
     for shape in [(32, 32), (32, 64), (64, 64), (16, 32), (16, 64)]:
         assert iwpp.iwpp_tile_shape_supported(*shape)
@@ -113,8 +113,8 @@ def test_host_argument_errors_return_before_any_launch(iwpp):
         p = iwpp.iwpp_default_plan()
         p.tile_h, p.tile_w, p.local_solver, p.value_levels = th, tw, solver, levels
         assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
-    # the cooperative solver takes no sweeps and at most 4 CTAs per SM
-    for kw in [{"sweeps": 1}, {"revisit_sweeps": 2}, {"blocks_per_sm": 6}]:
+    # the cooperative solver takes no revisit sweeps and at most 5 CTAs per SM
+    for kw in [{"revisit_sweeps": 2}, {"blocks_per_sm": 6}]:
         p = iwpp.iwpp_default_plan()
         p.tile_h, p.tile_w, p.local_solver = 64, 64, 2
         for k, v in kw.items():

@@ -112,7 +112,8 @@ def test_mixed_batch_random_schedule(iw, oracle_lib):
 
 def test_coop_batch_with_schedule(iw, oracle_lib):
     """A uniform batch under the cooperative solver with an explicit tile order (repeated and
-    missing ids) and per-tile sweep counts (which the cooperative solver does not run)."""
+    missing ids) and per-tile sweep counts 0..4 (run by the cooperative scan kernel on whole
+    64 x 64 tiles)."""
     cases = [synth.sparse_seed_case(700, 1100, nblobs=30, nseeds=6, image_idx=i) for i in range(3)]
     p = iw.iwpp_default_batch_plan()
     p.tile_h, p.tile_w, p.local_solver = 64, 64, 2

@@ -167,3 +167,32 @@ def test_block_labels_and_roundtrip(iw, tmp_path):
     assert s2 is not None and torch.equal(s.params, s2.params)
     (tmp_path / "w.bin").write_bytes(b"junk")
     assert learned.LearnedScheduler.load(str(tmp_path / "w.bin")) is None
+
+
+def test_full_512_image_learned_batch_matches_oracle(iw):
+    """The 512-image uneven batch (the learned schedule's test batch: sides log-uniform in
+    256..4096, u8/u16, h-dome dilations and fill-holes) reconstructed with a schedule from an
+    estimator trained on labels of the 512^2, 4096^2 (conn 8 and 4) and 16384^2 workloads,
+    then checked image by image against the oracle on the host's cores."""
+    import os
+    import oracle
+    from paper_1605_00930_gb300 import learned
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    c2 = synth.tissue_case()
+    sets = [[synth.noise_blur_case()], [c2], [synth.Case(c2.marker, c2.mask, 4, "dilate")],
+            [synth.sparse_seed_case()]]
+    sch, report = learned.train_from_workloads([_items(s) for s in sets], n_samples=50000, epochs=60)
+    assert report["mae_logwork"] <= report["mae_logwork_const"]
+    del sets
+    cases = synth.mixed_batch(512, workload_id=5, workers=min(16, cores))
+    items = _items(cases)
+    B = iw.Batch(items)
+    order, sweeps = sch.schedule(B)
+    assert B(order=order, sweeps=sweeps) == 0
+    assert B.status() == 0
+    outs = [m.cpu().numpy() for m, _, _, _ in items]
+    del items, B
+    exps = oracle.reconstruct_many([(c.marker, c.mask, c.conn, c.op) for c in cases], threads=cores)
+    for i, (got, exp) in enumerate(zip(outs, exps)):
+        assert np.array_equal(got, exp), f"image {i} {cases[i].mask.shape} {cases[i].mask.dtype} {cases[i].op} differs"

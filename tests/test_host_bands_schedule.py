@@ -4,7 +4,9 @@ against a simulated image on the CPU. The simulation is the column form of the p
 solved with their neighbour rows as fixed sources, exactly as iwpp_reconstruct_host solves
 its bands on the device. When the schedule says no band is left to visit, the banded result
 must equal the reconstruction of the whole column (and every band must have been visited),
-also when a run is interrupted after any band and repeated on the partly processed rows."""
+also when a run is interrupted after any band and repeated on the partly processed rows; the
+guess of the next band made while a band is solved (the band copied ahead) must be the band
+the schedule then returns whenever the solved band changed."""
 import os
 import subprocess
 
@@ -54,13 +56,19 @@ int main() {
         for (int pass = 0; pass < 2; pass++) {
             iwpp::BandSchedule order(nb);
             long here = 0;
-            for (long b = order.next(); b >= 0; b = order.next()) {
+            for (long b = order.next(); b >= 0;) {
                 if (pass == 0 && stop_after >= 0 && here == stop_after) break;
                 const int a = (int)b * band, e = std::min(n, a + band);
-                order.visited(b, solve(J, I, a, e));
+                // the guess of the next band made while b is solved is exact when b changes
+                const long guess = order.peek_after_change(b);
+                const bool ch = solve(J, I, a, e);
+                order.visited(b, ch);
                 seen[b] = 1;
                 here++;
                 if (++visits > 100000) { printf("no termination\n"); return 1; }
+                const long nxt = order.next();
+                if (ch && nxt != guess) { printf("trial %d: guess %ld, next %ld\n", trial, guess, nxt); return 1; }
+                b = nxt;
             }
             if (stop_after < 0) break;
         }

@@ -253,8 +253,11 @@ class Forms:
         stream = torch.cuda.current_stream()
         # one uncaptured call of each form first (kernel attributes, schedule buffers)
         self.Bs(stream=stream)
-        self.order, self.sweeps = sch.schedule(self.Bl, stream) if sch is not None else (None, None)
-        self.Bl(order=self.order, sweeps=self.sweeps, stream=stream)
+        if sch is not None:
+            if sch.reconstruct(self.Bl, stream) != 0:
+                raise RuntimeError("learned batch call failed")
+        else:
+            self.Bl(stream=stream)
         torch.cuda.synchronize()
         db.restore()
         self.g = {
@@ -265,17 +268,13 @@ class Forms:
         }
 
     def _scan(self, B, sch, s):
-        if sch is not None:
-            sch.schedule(B, s)
-            rc = B.phase("scan", order=self.order, sweeps=self.sweeps, stream=s)
-        else:
-            rc = B.phase("scan", stream=s)
+        # the learned form: schedule made inside the batch call (features from the scan kernel)
+        rc = sch.reconstruct(B, s, phases=1) if sch is not None else B.phase("scan", stream=s)
         if rc != 0:
             raise RuntimeError(f"batch scan phase failed: {rc}")
 
     def _drain(self, B, sch, s):
-        rc = B.phase("drain", order=self.order if sch is not None else None,
-                     sweeps=self.sweeps if sch is not None else None, stream=s)
+        rc = sch.reconstruct(B, s, phases=2) if sch is not None else B.phase("drain", stream=s)
         if rc != 0:
             raise RuntimeError(f"batch drain phase failed: {rc}")
 
@@ -290,8 +289,13 @@ class Forms:
         n = len(self.db.items)
         if form == "plain":
             return 2 * n
-        sched = ((n + 31) // 32 + 5) if form == "batched_learned" else 0
-        return sched + iwpp.iwpp_batch_launch_count(n, 3)
+        if form == "batched_static":
+            return iwpp.iwpp_batch_launch_count(n, 3)
+        fused = (self.plan.local_solver == iwpp.IWPP_SOLVER_COOP and self.plan.tile_h == 64 and
+                 self.plan.tile_w == 64 and len({c.conn for c in self.db.cases}) == 1)
+        if fused:   # features in the scan
+            return iwpp.iwpp_batch_launch_count(n, 7)
+        return (n + 31) // 32 + 5 + iwpp.iwpp_batch_launch_count(n, 3)
 
     def run(self, form: str, flush, ev=None):
         """One step of `form` on the current stream (events: start, after scan, end)."""
@@ -532,11 +536,7 @@ def run_ours(args, rank: int, world: int):
     def e2e_step():
         db.marker.copy_(hm, non_blocking=True)
         db.mask.copy_(hI, non_blocking=True)
-        if sch is not None:
-            order, sweeps = sch.schedule(F.Bl, stream)
-            rc = F.Bl(order=order, sweeps=sweeps, stream=stream)
-        else:
-            rc = F.Bs(stream=stream)
+        rc = sch.reconstruct(F.Bl, stream) if sch is not None else F.Bs(stream=stream)
         if rc != 0:
             raise RuntimeError(f"batch call failed: {rc}")
         ho.copy_(db.marker, non_blocking=True)
@@ -567,8 +567,9 @@ def run_ours(args, rank: int, world: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8/u16 (16-bit integer lanes)", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "images": len(head_cases),
                    "pixels_per_step": db.pixels,
-                   "form": ("batched + learned schedule: features, MLP and tile order, then one persistent "
-                            "launch over every image; both replayed from CUDA graphs" if sch is not None else
+                   "form": ("batched + learned schedule: one iwpp_reconstruct_batch_learned call (features "
+                            "out of the scan kernel, MLP, tile order, one persistent launch over every image), "
+                            "replayed from CUDA graphs" if sch is not None else
                             "batched, static tile order, CUDA graphs"),
                    "plan": plan.as_dict(),
                    "l2": "flushed before every timed step (256 MiB write); the inputs also exceed L2",
@@ -587,8 +588,8 @@ def run_ours(args, rank: int, world: int):
                 "h2d_bytes_per_step": 2 * db.nbytes, "d2h_bytes_per_step": db.nbytes,
                 "ms_per_step": round(e2e_ms, 3),
                 "form": ("per step: pinned H2D of every marker and mask (two arena copies), the learned "
-                         "schedule and the batch call through the C ABI, D2H of every result; L2 flushed "
-                         "before each step; CUDA events around the step")},
+                         "batch call through the C ABI (iwpp_reconstruct_batch_learned), D2H of every result; "
+                         "L2 flushed before each step; CUDA events around the step")},
         "gpu_launches": F.launches(form) * args.steps,
         "clocks": cs.summary(t0, t1),
         "estimator": estimator,

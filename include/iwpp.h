@@ -252,7 +252,8 @@ IWPP_API int iwpp_reconstruct_batch_phase(const iwpp_image *imgs, int n, const i
                                           void *stream);
 
 /* Kernel launches one iwpp_reconstruct_batch_phase call with n images makes (-1 for a
- * bad argument). Host-only call. */
+ * bad argument); phases + 4: one iwpp_reconstruct_batch_learned call whose features come
+ * out of the scan kernel. Host-only call. */
 IWPP_API int iwpp_batch_launch_count(int n, int phases);
 
 /*
@@ -350,6 +351,37 @@ IWPP_API int iwpp_mlp_train(float *params, float *adam_m, float *adam_v, float *
 IWPP_API int iwpp_schedule_from_predictions(const iwpp_image *imgs, int n, const iwpp_plan *plan,
                                             const float *preds, uint32_t *tile_order, uint8_t *tile_sweeps,
                                             void *sched_ws, size_t sws_bytes, void *stream);
+
+/* Byte offset of the features (float[nblocks][IWPP_NFEAT]) inside a scheduling workspace
+ * of this batch and plan (the array iwpp_reconstruct_batch_learned fills), or -1 for a bad
+ * argument. Host-only call. */
+IWPP_API int64_t iwpp_sched_features_offset(const iwpp_image *imgs, int n, const iwpp_plan *plan);
+
+/*
+ * A batch reconstructed with the learned schedule made inside the call (growth direction
+ * (4) in one call; the paper has no counterpart). When the plan's tiles are the feature
+ * blocks (the cooperative solver's 64 x 64 tiles) and the batch does not mix
+ * connectivities, the scan kernel computes each tile's features from the pixels it loads
+ * anyway (no separate pass over the images); then MLP inference, the tile order and the
+ * sweep counts as iwpp_schedule_learned makes them; then a pass that runs the sweep pairs
+ * of the tiles with a non-zero count (and notifies the neighbours they can raise); then
+ * the initial frontier is queued in the learned order and drained as in
+ * iwpp_reconstruct_batch_sched. Other plans: iwpp_schedule_learned, then
+ * iwpp_reconstruct_batch_sched. The result is identical to iwpp_reconstruct_batch.
+ *   params        device float[IWPP_MLP_PARAMS]
+ *   tile_order    device uint32[ntiles], tile_sweeps device uint8[ntiles]: receive the schedule
+ *   sched_ws      device, 256-byte aligned, iwpp_sched_workspace_bytes(imgs, n, plan) bytes;
+ *                 receives the features and predictions
+ *   phases        1: everything up to the persistent drain; 2: the drain alone (after a
+ *                 phases = 1 call with identical arguments on the same stream); 3: the
+ *                 whole call
+ *   workspace     as iwpp_reconstruct_batch
+ * No host synchronisation and no allocation: capturable in a CUDA graph.
+ */
+IWPP_API int iwpp_reconstruct_batch_learned(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                            const float *params, uint32_t *tile_order, uint8_t *tile_sweeps,
+                                            void *sched_ws, size_t sws_bytes, int phases, void *workspace,
+                                            size_t ws_bytes, void *stream);
 
 /* Features, MLP inference and schedule in one call (all on `stream`, no host sync). */
 IWPP_API int iwpp_schedule_learned(const iwpp_image *imgs, int n, const iwpp_plan *plan, const float *params,

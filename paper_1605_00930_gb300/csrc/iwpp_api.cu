@@ -116,7 +116,8 @@ static cudaError_t ensure_smem_attr(int shape, int v, size_t bytes) {
     const KernelSet &k = kernels(shape, v);
     const int want = (int)(bytes < 100 * 1024 ? 100 * 1024 : bytes);
     cudaError_t e;
-    for (void (*f)(EngineArgs) : {k.scan, k.drain, k.reg.scan, k.reg.drain, k.reg.drain_hi, k.coop.scan, k.coop.drain}) {
+    for (void (*f)(EngineArgs) : {k.scan, k.drain, k.reg.scan, k.reg.drain, k.reg.drain_hi, k.coop.scan, k.coop.drain,
+                                  k.coop.scan_sweeps, k.coop.scan_feats}) {
         if (!f) continue;
         e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e != cudaSuccess) return e;
@@ -142,8 +143,8 @@ static void (*drain_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
     if (p.local_solver != IWPP_SOLVER_REGISTER) return k.drain;
     return p.blocks_per_sm > kRegBlocks ? k.reg.drain_hi : k.reg.drain;
 }
-static void (*scan_fn(const iwpp_plan &p, const KernelSet &k))(EngineArgs) {
-    if (p.local_solver == IWPP_SOLVER_COOP) return k.coop.scan;
+static void (*scan_fn(const iwpp_plan &p, const KernelSet &k, bool sweeps))(EngineArgs) {
+    if (p.local_solver == IWPP_SOLVER_COOP) return sweeps && k.coop.scan_sweeps ? k.coop.scan_sweeps : k.coop.scan;
     return p.local_solver == IWPP_SOLVER_REGISTER ? k.reg.scan : k.scan;
 }
 static size_t drain_smem(const iwpp_plan &p, const KernelSet &k) {
@@ -267,6 +268,8 @@ static void fill_common(EngineArgs &a, const iwpp_plan &p, uint8_t *base, size_t
     a.nlevels = p.value_levels > 1 ? (uint32_t)p.value_levels : 1u;
     a.lvl = nullptr;
     a.tile_img = nullptr;
+    a.feats = nullptr;
+    a.sweep_only = 0;
 }
 
 // ---- single image ------------------------------------------------------------------------------
@@ -333,7 +336,7 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
         const int sms = device_sm_count();
         const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
         const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
-        scan_fn(p, k)<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
+        scan_fn(p, k, p.sweeps > 0)<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
     }
     if (phases & kPhaseDrain) drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
@@ -428,8 +431,9 @@ size_t batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *pla
 
 int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, const uint32_t *order,
                       const uint8_t *tile_sweeps, uint32_t *tile_work, void *ws, size_t ws_bytes,
-                      cudaStream_t stream, int phases) {
+                      cudaStream_t stream, int phases, const LearnedCall *learned) {
     if (phases < 1 || phases > 3) return IWPP_ERR_ARG;
+    if (learned && (!learned->params || !learned->order || !learned->sweeps || !learned->sws)) return IWPP_ERR_ARG;
     iwpp_plan p;
     if (plan_in) p = *plan_in; else default_batch_plan(&p);
     if (!plan_valid(p) || p.value_levels > 1) return IWPP_ERR_ARG;   // batches: one FIFO
@@ -461,6 +465,14 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     const KernelSet &k = kernels(shape, variant);
     const size_t smem = k.smem ? k.smem(a.qcap) : drain_smem(p, k);
     if (ensure_smem_attr(shape, variant, smem) != cudaSuccess) return IWPP_ERR_CUDA;
+    // learned: features from the scan kernel when the plan's tiles are the feature blocks
+    // (cooperative 64 x 64 tiles; not the mixed-kind build), else a features pass first
+    const bool fused = learned && p.local_solver == IWPP_SOLVER_COOP && k.coop.scan_feats &&
+                       p.tile_h == IWPP_FEATURE_BLOCK && p.tile_w == IWPP_FEATURE_BLOCK;
+    if (learned) {
+        order = learned->order;
+        tile_sweeps = learned->sweeps;
+    }
 
     if ((phases & kPhaseScan) == 0) {   // drain only: the prepared workspace is reused
         drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
@@ -488,7 +500,29 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     const int sms = device_sm_count();
     const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
     const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
-    scan_fn(p, k)<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
+    if (learned && !fused) {   // features, MLP and order before the scan, which runs the sweeps
+        const int rc = schedule_batch(imgs, n, p, learned->params, learned->order, learned->sweeps, learned->sws,
+                                      learned->sws_bytes, stream, 7);
+        if (rc != IWPP_OK) return rc;
+    }
+    if (fused) {
+        // scan with features (no sweeps yet) -> MLP and order -> sweeps-only pass
+        a.feats = sched_features(imgs, n, p, learned->sws, learned->sws_bytes);
+        if (!a.feats) return IWPP_ERR_WORKSPACE;
+        a.tile_sweeps = nullptr;
+        k.coop.scan_feats<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
+        if (cudaGetLastError() != cudaSuccess) return IWPP_ERR_CUDA;
+        const int rc = schedule_batch(imgs, n, p, learned->params, learned->order, learned->sweeps, learned->sws,
+                                      learned->sws_bytes, stream, 6);
+        if (rc != IWPP_OK) return rc;
+        a.feats = nullptr;
+        a.tile_sweeps = learned->sweeps;
+        a.sweep_only = 1;
+        k.coop.scan_sweeps<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
+        a.sweep_only = 0;
+    } else {
+        scan_fn(p, k, p.sweeps > 0 || tile_sweeps != nullptr)<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
+    }
     const uint32_t cgrid = (L.ntiles + 255) / 256 < (uint32_t)(sms * 8) ? (L.ntiles + 255) / 256 : (uint32_t)(sms * 8);
     compact_kernel<<<cgrid, 256, 0, stream>>>(a);
     finalize_queue_kernel<<<cgrid, 256, 0, stream>>>(a);
@@ -496,9 +530,13 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
 }
 
-// Kernel launches one batch call makes (for launch accounting by callers).
+// Kernel launches one batch call makes (for launch accounting by callers); bit 2 of
+// `phases`: a learned call with the features in the scan (the schedule's table chunks, MLP,
+// keys, bucket scan and scatter, and the sweeps-only pass come on top).
 int batch_launches(int n, int phases) {
-    const int prep = (n + kDescChunk - 1) / kDescChunk + 4;   // table chunks, tile map, scan, compact, finalize
+    const int chunks = (n + kDescChunk - 1) / kDescChunk;
+    int prep = chunks + 4;   // table chunks, tile map, scan, compact, finalize
+    if (phases & 4) prep += chunks + 5;
     return ((phases & kPhaseScan) ? prep : 0) + ((phases & kPhaseDrain) ? 1 : 0);
 }
 
@@ -587,8 +625,17 @@ extern "C" int iwpp_reconstruct_batch_phase(const iwpp_image *imgs, int n, const
 }
 
 extern "C" int iwpp_batch_launch_count(int n, int phases) {
-    if (n < 1 || phases < 1 || phases > 3) return -1;
+    if (n < 1 || (phases & 3) == 0 || phases > 7) return -1;
     return iwpp::batch_launches(n, phases);
+}
+
+extern "C" int iwpp_reconstruct_batch_learned(const iwpp_image *imgs, int n, const iwpp_plan *plan,
+                                              const float *params, uint32_t *tile_order, uint8_t *tile_sweeps,
+                                              void *sched_ws, size_t sws_bytes, int phases, void *workspace,
+                                              size_t ws_bytes, void *stream) {
+    const iwpp::LearnedCall lc = {params, tile_order, tile_sweeps, sched_ws, sws_bytes};
+    return iwpp::reconstruct_batch(imgs, n, plan, nullptr, nullptr, nullptr, workspace, ws_bytes,
+                                   static_cast<cudaStream_t>(stream), phases, &lc);
 }
 
 extern "C" int iwpp_sync_status(const void *workspace, void *stream) {

@@ -10,6 +10,7 @@
 // images and uniform batches; the mixed build dispatches on each tile's image kind.
 #pragma once
 
+#include "iwpp_feat.cuh"
 #include "iwpp_regtile.cuh"
 
 namespace iwpp {
@@ -21,6 +22,8 @@ struct CoopShared {
     uint32_t rows[kWarpsPerCta][2][32];   // each strip's first and last row, per lane
     uint32_t misc[16];                    // the CTA tile's notification values (3 x 3 grid)
     uint32_t tile, redo;
+    uint32_t fv[kWarpsPerCta][16];        // scan with features: each strip's feature sums
+    unsigned long long fq[kWarpsPerCta][2];
 };
 
 template <typename T, int CONN>
@@ -236,11 +239,58 @@ __global__ void __launch_bounds__(kThreads, MIXED ? kRegBlocks : kCoopBlocks) dr
 // (a.tile_sweeps[t], else a.sweeps), the strips exchanging their boundary rows after each
 // pair, store what changed and notify the neighbours whose halo pixels the tile can now
 // raise; queue the tile if one of its pixels can still rise.
-template <typename T, int CONN>
+// Feature sums of one strip (iwpp_feat.cuh) into C.fv[w] / C.fq[w]: every pixel of the strip
+// inside the image, with its right neighbour (in the tile) and the one below (the next strip's
+// first row is the halo row `ib`; below the tile's last row there is none).
+template <typename RT>
+__device__ __forceinline__ void strip_features(const ImageView &im, int y0, int x0, const uint32_t (&J)[RT::kRows],
+                                               const uint32_t (&I)[RT::kRows], uint32_t ib, CoopShared &C, int w,
+                                               int lane) {
+    constexpr int TH = RT::kRows;
+    FeatAcc fa;
+    const bool u16 = RT::wide(im);
+    const uint32_t M = u16 ? 0xFFFFu : 0xFFu, thr = 16u * (M / 255u);
+    const int gx = x0 + 2 * lane;
+    const bool c0 = gx < im.W, c1 = gx + 1 < im.W, c2 = lane < 31 && gx + 2 < im.W;
+#pragma unroll
+    for (int r = 0; r < TH; r++) {
+        if (y0 + r < im.H) {   // warp-uniform
+            const uint32_t iv = I[r], jv = J[r];
+            const uint32_t nxt = __shfl_down_sync(0xffffffffu, iv, 1);
+            const bool down = y0 + r + 1 < im.H && (r + 1 < TH || w < kWarpsPerCta - 1);
+            const uint32_t bv = r + 1 < TH ? I[r + 1 < TH ? r + 1 : r] : ib;
+            const uint32_t ie = iv & 0xFFFFu, io = iv >> 16;
+            if (c0) {
+                feat_pixel(fa, ie, jv & 0xFFFFu, u16);
+                const uint32_t g = (c1 ? (uint32_t)abs((int)io - (int)ie) : 0u) +
+                                   (down ? (uint32_t)abs((int)(bv & 0xFFFFu) - (int)ie) : 0u);
+                fa.edges += g > thr;
+            }
+            if (c1) {
+                feat_pixel(fa, io, jv >> 16, u16);
+                const uint32_t g = (c2 ? (uint32_t)abs((int)(nxt & 0xFFFFu) - (int)io) : 0u) +
+                                   (down ? (uint32_t)abs((int)(bv >> 16) - (int)io) : 0u);
+                fa.edges += g > thr;
+            }
+        }
+    }
+    uint32_t v[16];
+    unsigned long long q0, q1;
+    feat_reduce(fa, v, q0, q1);
+    if (lane < 16) C.fv[w][lane] = v[lane];
+    if (lane == 0) {
+        C.fq[w][0] = q0;
+        C.fq[w][1] = q1;
+    }
+}
+
+template <typename T, int CONN, bool SWEEPS, bool FEATS = false>
 __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem,
                                CoopShared &C, int w, int lane) {
     constexpr int TH = kCoopStrip;
     using RT = RegTile<T, CONN, TH>;
+    const int sweeps = !SWEEPS ? 0 : a.tile_sweeps ? (int)a.tile_sweeps[t] : a.sweeps;   // CTA-uniform
+    if (SWEEPS && a.sweep_only && sweeps == 0) return;   // the sweeps-only pass: nothing to do here
     const long long c0 = clock64();
     const typename RT::Smem s = RT::carve(wsmem);
     const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
@@ -249,10 +299,10 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     const int y0 = ty * kCoopRows + TH * w, x0 = tx * RT::TW;
     uint32_t J[TH], I[TH], jt, jb, it, ib;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+    if constexpr (FEATS) strip_features<RT>(im, y0, x0, J, I, ib, C, w, lane);
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
-    const int sweeps = a.tile_sweeps ? (int)a.tile_sweeps[t] : a.sweeps;   // CTA-uniform
     uint32_t rows = 0;
     for (int k = 0; k < sweeps; k++) {
         rows |= RT::sweep_raster(hx, J, I, jt, lane);
@@ -267,6 +317,16 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     const bool can = RT::improvable(hx, J, I, jt, jb, lane);
     const int any_bad = __syncthreads_or(bad);
     const int any_can = __syncthreads_or(can);
+    if constexpr (FEATS) {   // the strips' sums are in C.fv / C.fq (barriers above)
+        if (w == 0 && lane < 16) {
+            uint32_t v[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) v[k] = C.fv[0][k] + C.fv[1][k] + C.fv[2][k] + C.fv[3][k];
+            const unsigned long long q0 = C.fq[0][0] + C.fq[1][0] + C.fq[2][0] + C.fq[3][0];
+            const unsigned long long q1 = C.fq[0][1] + C.fq[1][1] + C.fq[2][1] + C.fq[3][1];
+            a.feats[(size_t)t * 16 + lane] = block_feature(lane, v, q0, q1, RT::wide(im) ? 0xFFFFu : 0xFFu);
+        }
+    }
     if (sweeps > 0 && __syncthreads_or(rows != 0)) {
         RT::store(im, y0, x0, J, rows, lane);
         if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
@@ -293,8 +353,11 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     __syncthreads();   // the strips' shared halo buffers are reloaded for the next tile
 }
 
-template <typename T, int CONN, bool MIXED>
-__global__ void __launch_bounds__(kThreads) scan_coop_kernel(EngineArgs a) {
+// SWEEPS: the build that runs sweep pairs (plans with sweeps, per-tile sweep counts); the
+// other one only checks and collects the frontier, with few enough registers for 8 CTAs per
+// SM (the scan is a pass over every pixel: loads in flight are what it needs).
+template <typename T, int CONN, bool MIXED, bool SWEEPS, bool FEATS = false>
+__global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : (FEATS ? 5 : 8)) scan_coop_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -303,14 +366,14 @@ __global__ void __launch_bounds__(kThreads) scan_coop_kernel(EngineArgs a) {
     for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const ImageView &im = image_of(a, t);
         if (!MIXED) {
-            scan_tile_coop<T, CONN>(a, im, t, wsmem, C, w, lane);
+            scan_tile_coop<T, CONN, SWEEPS, FEATS>(a, im, t, wsmem, C, w, lane);
             continue;
         }
         switch (im.kind) {
-            case 0: scan_tile_coop<uint8_t, 4>(a, im, t, wsmem, C, w, lane); break;
-            case 1: scan_tile_coop<uint16_t, 4>(a, im, t, wsmem, C, w, lane); break;
-            case 2: scan_tile_coop<uint8_t, 8>(a, im, t, wsmem, C, w, lane); break;
-            default: scan_tile_coop<uint16_t, 8>(a, im, t, wsmem, C, w, lane); break;
+            case 0: scan_tile_coop<uint8_t, 4, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
+            case 1: scan_tile_coop<uint16_t, 4, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
+            case 2: scan_tile_coop<uint8_t, 8, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
+            default: scan_tile_coop<uint16_t, 8, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
         }
     }
 }

@@ -137,6 +137,8 @@ struct EngineArgs {
     uint32_t nlevels;            // 1: one FIFO ring; >1: one ring per value level (queue + L * ntiles)
     LevelCtr *lvl;               // nlevels counters (value-ordered mode)
     const uint32_t *tile_img;    // batch: index of each tile's image in imgs (else nullptr)
+    float *feats;                // learned batches: per-tile features out of the scan (64 x 64 tiles)
+    int sweep_only;              // scan: skip tiles whose sweep count is 0 (a second, sweeps-only pass)
 };
 
 // ---- small device helpers ------------------------------------------------------------------

@@ -20,6 +20,8 @@ struct RegKernelSet {
     void (*drain)(EngineArgs);
     void (*drain_hi)(EngineArgs);
     size_t (*smem)(uint32_t);
+    void (*scan_sweeps)(EngineArgs);   // scan build that runs sweeps (null: `scan` runs them)
+    void (*scan_feats)(EngineArgs);    // scan build that also writes each tile's features (or null)
 };
 constexpr int kRegBlocks = 4, kRegHiBlocks = 6;
 #ifndef IWPP_COOP_MINB
@@ -43,8 +45,23 @@ size_t batch_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *pla
 // Phases of a call: bit 0 = workspace reset + scan (batches: table upload, scan, queue
 // compaction), bit 1 = persistent drain.
 enum { kPhaseScan = 1, kPhaseDrain = 2 };
+// A learned batch call: the schedule (tile order, sweep counts) is made inside the call, from
+// features written by the scan kernel when the plan's tiles are the feature blocks.
+struct LearnedCall {
+    const float *params;
+    uint32_t *order;    // out: tile order, uint32[ntiles]
+    uint8_t *sweeps;    // out: sweep counts, uint8[ntiles]
+    void *sws;
+    size_t sws_bytes;
+};
 int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan, const uint32_t *order,
                       const uint8_t *tile_sweeps, uint32_t *tile_work, void *ws, size_t ws_bytes,
-                      cudaStream_t stream, int phases);
+                      cudaStream_t stream, int phases, const LearnedCall *learned = nullptr);
 int batch_launches(int n, int phases);
+// The learned schedule's pieces a batch call drives (iwpp_sched.cu): the address of the
+// feature array in a scheduling workspace (null if the workspace is too small), and the
+// schedule itself (phases: 1 features, 2 MLP inference, 4 tile order and sweep counts).
+float *sched_features(const iwpp_image *imgs, int n, const iwpp_plan &p, void *sws, size_t sws_bytes);
+int schedule_batch(const iwpp_image *imgs, int n, const iwpp_plan &p, const float *params, uint32_t *order,
+                   uint8_t *sweeps, void *sws, size_t sws_bytes, cudaStream_t stream, int phases);
 }  // namespace iwpp

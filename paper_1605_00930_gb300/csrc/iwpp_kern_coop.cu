@@ -8,15 +8,19 @@ namespace iwpp {
 template <typename T, int CONN, bool MIXED = false>
 static RegKernelSet coop_set() {
     RegKernelSet k;
-    k.scan = scan_coop_kernel<T, CONN, MIXED>;
+    k.scan = scan_coop_kernel<T, CONN, MIXED, false>;
     k.drain = drain_coop_kernel<T, CONN, MIXED>;
-    k.drain_hi = nullptr;   // one build: 4 CTAs of 4 warps per SM
+    k.drain_hi = nullptr;   // one build of the persistent kernel
     k.smem = &coop_smem_fn<T, CONN>;
+    k.scan_sweeps = scan_coop_kernel<T, CONN, MIXED, true>;
+    // features in the scan: not for the mixed-kind build (its scan would inline four copies)
+    if constexpr (MIXED) k.scan_feats = nullptr;
+    else k.scan_feats = scan_coop_kernel<T, CONN, false, false, true>;
     return k;
 }
 
 RegKernelSet coop_kernel_set(int th, int tw, int v) {
-    RegKernelSet none = {nullptr, nullptr, nullptr, nullptr};
+    RegKernelSet none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     if (th != kCoopRows || tw != RegTile<uint8_t, 8, kCoopStrip>::TW) return none;
     switch (v) {
         case 0: return coop_set<uint8_t, 4>();

@@ -12,11 +12,13 @@ static RegKernelSet reg_set() {
     k.drain = drain_reg_kernel<T, CONN, TH, LO>;
     k.drain_hi = drain_reg_kernel<T, CONN, TH, HI>;
     k.smem = &RegTile<T, CONN, TH>::smem_bytes;
+    k.scan_sweeps = nullptr;
+    k.scan_feats = nullptr;
     return k;
 }
 
 RegKernelSet reg_kernel_set(int th, int tw, int v) {
-    RegKernelSet none = {nullptr, nullptr, nullptr, nullptr};
+    RegKernelSet none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     if (th != 16 || tw != RegTile<uint8_t, 8, 16>::TW) return none;
     switch (v) {
         case 0: return reg_set<uint8_t, 4, 16>();
@@ -29,6 +31,8 @@ RegKernelSet reg_kernel_set(int th, int tw, int v) {
             k.drain = drain_reg_mixed_kernel<16, kRegBlocks>;
             k.drain_hi = drain_reg_mixed_kernel<16, kRegHiBlocks>;
             k.smem = &RegTile<uint16_t, 8, 16>::smem_bytes;
+            k.scan_sweeps = nullptr;
+            k.scan_feats = nullptr;
             return k;
         }
         default: return none;

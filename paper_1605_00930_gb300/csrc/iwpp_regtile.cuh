@@ -46,6 +46,7 @@ template <typename T, int CONN, int TH>
 struct RegTile {
     static_assert(TH >= 2 && TH <= 32, "tile rows");
     static constexpr int TW = 64;
+    static constexpr int kRows = TH;
     // 16-bit pixels?
     static __device__ __forceinline__ bool wide(const ImageView &im) {
         if constexpr (std::is_same<T, AnyPix>::value) return (im.kind & 1u) != 0;

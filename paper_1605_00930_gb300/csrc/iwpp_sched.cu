@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/iwpp.h"
+#include "iwpp_feat.cuh"
 #include "iwpp_host.h"
 
 namespace iwpp {
@@ -63,27 +64,6 @@ __device__ __forceinline__ int find_image(const SchedImage *tab, int n, uint32_t
 // Exact integer sums per lane (8-bit packed histogram counters: at most 128 pixels per lane),
 // warp reductions, then lane 0 converts. Rows are read four at a time so that several loads
 // are in flight per warp; the edge test of a row needs the next row's mask, so it lags by one.
-struct FeatAcc {
-    uint32_t h03 = 0, h47 = 0;   // histogram bins, 8 bits each
-    uint32_t seeds = 0, edges = 0, sI = 0, sJ = 0, sD = 0, n = 0;
-    unsigned long long sI2 = 0, sJ2 = 0;
-};
-
-__device__ __forceinline__ void feat_pixel(FeatAcc &a, uint32_t i, uint32_t j, bool u16) {
-    const uint32_t d = i > j ? i - j : 0u;
-    const uint32_t d8 = u16 ? d >> 8 : d;
-    const uint32_t bin = d8 == 0 ? 0u : min(7u, 32u - (uint32_t)__clz(d8));
-    const uint32_t inc = 1u << (8 * (bin & 3));
-    if (bin < 4) a.h03 += inc; else a.h47 += inc;
-    a.seeds += (i == j && j > 0);
-    a.sI += i;
-    a.sJ += j;
-    a.sD += d;
-    a.sI2 += (unsigned long long)i * i;
-    a.sJ2 += (unsigned long long)j * j;
-    a.n++;
-}
-
 // Pixels (y, x) and (y, x + 1) of plane p (flipped), loaded with clamped addresses; the
 // caller masks the ones outside the block.
 __device__ __forceinline__ void feat_load(const SchedImage &im, const uint8_t *p, int y, int x, uint32_t &e,
@@ -223,43 +203,9 @@ __global__ void __launch_bounds__(256) features_kernel(const SchedImage *tab, in
         }
 
         uint32_t v[16];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            v[q] = __reduce_add_sync(0xffffffffu, (a.h03 >> (8 * q)) & 0xFFu);
-            v[4 + q] = __reduce_add_sync(0xffffffffu, (a.h47 >> (8 * q)) & 0xFFu);
-        }
-        v[8] = __reduce_add_sync(0xffffffffu, a.seeds);
-        v[9] = __reduce_add_sync(0xffffffffu, a.edges);
-        v[10] = __reduce_add_sync(0xffffffffu, a.sI);   // < 2^32: 4096 pixels x 65535
-        v[12] = __reduce_add_sync(0xffffffffu, a.sJ);
-        v[14] = __reduce_add_sync(0xffffffffu, a.sD);
-        v[15] = __reduce_add_sync(0xffffffffu, a.n);
-        unsigned long long sI2 = a.sI2, sJ2 = a.sJ2;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the sums
-            sI2 += __shfl_xor_sync(0xffffffffu, sI2, o);
-            sJ2 += __shfl_xor_sync(0xffffffffu, sJ2, o);
-        }
-        // Conversion in FP32 (FP64 is slow on this part) from exact integers: the variance
-        // numerator N * sum(x^2) - sum(x)^2 is exact in 64 bits (N <= 4096, x <= 65535),
-        // so no cancellation; every feature is within a few float ulps of the exact value.
-        if (lane < kNF) {
-            const uint32_t N = v[15];
-            const float fN = (float)N, NM = (float)N * (float)M;
-            const unsigned long long vI = (unsigned long long)N * sI2 - (unsigned long long)v[10] * v[10];
-            const unsigned long long vJ = (unsigned long long)N * sJ2 - (unsigned long long)v[12] * v[12];
-            float r;
-            switch (lane) {
-                case 10: r = (float)v[10] / NM; break;
-                case 11: r = sqrtf((float)vI) / NM; break;
-                case 12: r = (float)v[12] / NM; break;
-                case 13: r = sqrtf((float)vJ) / NM; break;
-                case 14: r = (float)v[14] / NM; break;
-                case 15: r = log2f(fN) / 12.f; break;
-                default: r = (float)v[lane] / fN; break;   // histogram, seeds, edges
-            }
-            out[(size_t)b * kNF + lane] = r;
-        }
+        unsigned long long sI2, sJ2;
+        feat_reduce(a, v, sI2, sJ2);
+        if (lane < kNF) out[(size_t)b * kNF + lane] = block_feature(lane, v, sI2, sJ2, M);
     }
 }
 
@@ -590,11 +536,31 @@ static int schedule_impl(const iwpp_image *imgs, int n, const iwpp_plan *plan_in
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
 }
 
+float *sched_features(const iwpp_image *imgs, int n, const iwpp_plan &p, void *sws, size_t sws_bytes) {
+    SchedLayout L;
+    if (!sws || ((uintptr_t)sws & 255) || !sched_layout(imgs, n, p, L, nullptr, nullptr) || sws_bytes < L.total)
+        return nullptr;
+    return reinterpret_cast<float *>(static_cast<uint8_t *>(sws) + L.feats);
+}
+
+int schedule_batch(const iwpp_image *imgs, int n, const iwpp_plan &p, const float *params, uint32_t *order,
+                   uint8_t *sweeps, void *sws, size_t sws_bytes, cudaStream_t stream, int phases) {
+    return schedule_impl(imgs, n, &p, params, nullptr, nullptr, order, sweeps, sws, sws_bytes, stream, phases);
+}
+
 }  // namespace iwpp
 
 // ---- C ABI ------------------------------------------------------------------------------------
 extern "C" int64_t iwpp_batch_block_count(const iwpp_image *imgs, int n) {
     return iwpp::count_blocks(imgs, n, nullptr);
+}
+
+extern "C" int64_t iwpp_sched_features_offset(const iwpp_image *imgs, int n, const iwpp_plan *plan) {
+    iwpp_plan p;
+    if (plan) p = *plan; else iwpp::default_batch_plan(&p);
+    if (!iwpp::plan_valid(p)) return -1;
+    iwpp::SchedLayout L;
+    return iwpp::sched_layout(imgs, n, p, L, nullptr, nullptr) ? (int64_t)L.feats : -1;
 }
 
 extern "C" size_t iwpp_sched_workspace_bytes(const iwpp_image *imgs, int n, const iwpp_plan *plan) {

@@ -83,6 +83,11 @@ _PROTOS = [
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("iwpp_batch_launch_count", ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    ("iwpp_reconstruct_batch_learned", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
+                                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("iwpp_sched_features_offset", ctypes.c_int64, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan)]),
     ("iwpp_batch_graph_create", ctypes.c_int, [ctypes.POINTER(Image), ctypes.c_int, ctypes.POINTER(Plan),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
@@ -243,6 +248,16 @@ def iwpp_reconstruct_batch_phase(imgs, plan, order_ptr, sweeps_ptr, work_ptr, ph
 
 def iwpp_batch_launch_count(n: int, phases: int = 3) -> int:
     return lib().iwpp_batch_launch_count(int(n), int(phases))
+
+
+def iwpp_reconstruct_batch_learned(imgs, plan, params_ptr, order_ptr, sweeps_ptr, sws_ptr, sws_bytes, phases,
+                                   ws_ptr, ws_bytes, stream) -> int:
+    return lib().iwpp_reconstruct_batch_learned(imgs, len(imgs), _pp(plan), params_ptr, order_ptr, sweeps_ptr,
+                                                sws_ptr, sws_bytes, int(phases), ws_ptr, ws_bytes, stream)
+
+
+def iwpp_sched_features_offset(imgs, plan=None) -> int:
+    return lib().iwpp_sched_features_offset(imgs, len(imgs), _pp(plan))
 
 
 def iwpp_batch_graph_create(imgs, plan, order_ptr, sweeps_ptr, ws_ptr, ws_bytes):

@@ -136,17 +136,39 @@ class LearnedScheduler:
         return Y
 
     # -- scheduling -----------------------------------------------------------------------
-    def schedule(self, batch: "iwpp.Batch", stream=None):
-        """Device tile order and sweep counts for `batch` (no host synchronisation)."""
+    def _buffers(self, batch):
         import torch
         dev = batch.ws.device
         if not hasattr(batch, "_sched_ws"):
             batch._sched_ws = iwpp.alloc_workspace(iwpp.iwpp_sched_workspace_bytes(batch.descs, batch.plan), dev)
             batch._order = torch.empty(batch.ntiles, dtype=torch.int32, device=dev)
             batch._sweeps = torch.empty(batch.ntiles, dtype=torch.uint8, device=dev)
+
+    def schedule(self, batch: "iwpp.Batch", stream=None):
+        """Device tile order and sweep counts for `batch` (no host synchronisation)."""
+        self._buffers(batch)
         iwpp.iwpp_schedule_learned(batch.descs, batch.plan, self.params, batch._order, batch._sweeps,
                                    batch._sched_ws, stream)
         return batch._order, batch._sweeps
+
+    def reconstruct(self, batch: "iwpp.Batch", stream=None, phases: int = 3) -> int:
+        """Reconstruct `batch` with the schedule made inside the call (iwpp_reconstruct_batch_learned:
+        features from the scan kernel under the default plan). Returns the host status; the
+        schedule lands in batch._order / batch._sweeps."""
+        import ctypes
+        self._buffers(batch)
+        P = ctypes.c_void_p
+        return iwpp.iwpp_reconstruct_batch_learned(
+            batch.descs, batch.plan, P(self.params.data_ptr()), P(batch._order.data_ptr()),
+            P(batch._sweeps.data_ptr()), P(batch._sched_ws.data_ptr()), batch._sched_ws.numel(), phases,
+            P(batch.ws.data_ptr()), batch.ws.numel(), iwpp._stream_handle(stream))
+
+    def features_of(self, batch: "iwpp.Batch"):
+        """The features the last reconstruct() call wrote (float32 [nblocks, 16], a view)."""
+        import torch
+        off = iwpp.iwpp_sched_features_offset(batch.descs, batch.plan)
+        nb = iwpp.iwpp_batch_block_count(batch.descs)
+        return batch._sched_ws[off:off + nb * iwpp.NFEAT * 4].view(torch.float32).view(nb, iwpp.NFEAT)
 
     # -- persistence ----------------------------------------------------------------------
     def save(self, path: str):
@@ -197,6 +219,7 @@ def train_from_workloads(item_sets, n_samples: int = 50000, epochs: int = 60, se
         "mae_logwork_const": float(np.mean(np.abs(base[0] - T[te, 0]))),
         "mae_sweeps": float(np.mean(np.abs(np.clip(np.rint(pred[:, 1]), 0, 8) - T[te, 1]))),
         "mae_sweeps_const": float(np.mean(np.abs(np.rint(base[1]) - T[te, 1]))),
+        "sweep_label_share": {str(o): round(float(np.mean(T[:, 1] == o)), 4) for o in SWEEP_OPTIONS},
     }
     sch.meta.update({"report": report})
     return sch, report

@@ -169,6 +169,70 @@ def test_block_labels_and_roundtrip(iw, tmp_path):
     assert learned.LearnedScheduler.load(str(tmp_path / "w.bin")) is None
 
 
+def _mixed8_cases(seed, n, side=300):
+    """u8 and u16 images of one connectivity (8): the batch kernel that reads the pixel size per
+    image; h-dome dilations and fill-holes; ragged sizes (partial 64 x 64 tiles)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        H, W = int(rng.integers(1, side)), int(rng.integers(1, side))
+        is16 = bool(rng.integers(0, 2))
+        f = synth.blob_field_u8(H, W, max(1, H * W // 2500), rng)
+        mask = synth.to_u16(f) if is16 else f
+        if i % 2 == 0:
+            out.append(synth.Case(synth.hdome_marker(mask, int(rng.integers(5, 50)) * (257 if is16 else 1)), mask,
+                                  8, "dilate"))
+        else:
+            out.append(synth.Case(synth.fillholes_marker(mask), mask, 8, "erode"))
+    return out
+
+
+@pytest.mark.parametrize("kind", ["mixed8", "mixed_conn", "u8"])
+def test_learned_batch_call_bit_exact_and_features(iw, oracle_lib, kind):
+    """iwpp_reconstruct_batch_learned: the schedule made inside the call (features from the scan
+    kernel for one connectivity; a features pass first when connectivities are mixed) gives
+    the oracle's result image by image, and the features it wrote equal the float64 oracle's."""
+    from paper_1605_00930_gb300 import learned
+    if kind == "mixed8":
+        cases = _mixed8_cases(41, 14)
+    elif kind == "mixed_conn":
+        cases = _cases(42, 10, side=300)
+    else:
+        cases = [synth.tissue_case(200 + 37 * i, 150 + 53 * i, nblobs=8, image_idx=i) for i in range(5)]
+    items = _items(cases)
+    sch = learned.LearnedScheduler(learned.init_params(5))
+    B = iw.Batch(items)
+    assert sch.reconstruct(B) == 0
+    assert B.status() == 0
+    for i, (c, (m, _, _, _)) in enumerate(zip(cases, items)):
+        assert np.array_equal(m.cpu().numpy(), oracle_lib.reconstruct(c.marker, c.mask, c.conn, c.op)), i
+    got = sch.features_of(B).cpu().numpy()
+    np.testing.assert_allclose(got, ofeat.batch_features(cases), rtol=1e-6, atol=1e-7)
+    o = B._order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(B.ntiles))
+
+
+def test_learned_batch_call_phases_and_sweeps(iw, oracle_lib):
+    """The call split into its two phases (prepare + scan + schedule, then the drain) gives the
+    whole call's result; with an MLP whose sweep output is large every tile runs sweep pairs in
+    the sweeps-only pass, bit-exact as well."""
+    from paper_1605_00930_gb300 import learned
+    cases = _mixed8_cases(43, 10)
+    p = learned.init_params(6)
+    n1 = 16 * 64 + 64 + 64 * 64 + 64        # offset of the last layer's weights [64][2]
+    p[n1 + 1:n1 + 128:2] = 0.0              # output 1 (sweep count) ignores the hidden layer ...
+    p[-1] = 3.0                             # ... and is 3 pairs for every tile
+    sch = learned.LearnedScheduler(p)
+    items = _items(cases)
+    B = iw.Batch(items)
+    assert sch.reconstruct(B, phases=1) == 0
+    assert sch.reconstruct(B, phases=2) == 0
+    assert B.status() == 0
+    assert np.all(B._sweeps.cpu().numpy() == 3)
+    for i, (c, (m, _, _, _)) in enumerate(zip(cases, items)):
+        assert np.array_equal(m.cpu().numpy(), oracle_lib.reconstruct(c.marker, c.mask, c.conn, c.op)), i
+
+
 def test_full_512_image_learned_batch_matches_oracle(iw):
     """The 512-image uneven batch (the learned schedule's test batch: sides log-uniform in
     256..4096, u8/u16, h-dome dilations and fill-holes) reconstructed with a schedule from an

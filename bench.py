@@ -459,11 +459,38 @@ def choose_plan(db, dev):
     return plan
 
 
+def run_profile(args):
+    """A lean run for profilers: the workload's batched static form only (default plan, no
+    autotuning, no other forms), W warm-up steps then K timed steps. The persistent drain of
+    timed step k is the library's drain launch number 2 + W + k of the process (0-based: the
+    two uncaptured set-up calls come first), which is what an ncu -k / -s / -c selection needs."""
+    import torch
+    from paper_1605_00930_gb300 import build as B
+    B.build()
+    from paper_1605_00930_gb300 import iwpp
+    cases = load_workload(args.workload)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    db = DeviceBatch(cases, dev)
+    F = Forms(db, None, iwpp.iwpp_default_batch_plan(), dev)
+    for _ in range(args.warmup):
+        db.restore()
+        flush.fill_(1)
+        F.run("batched_static", flush)
+    ts = F.timed("batched_static", flush, args.steps)
+    return {"profile_run": args.workload, "form": "batched_static", "steps": args.steps, "warmup": args.warmup,
+            "ms": [round(t[0], 4) for t in ts], "drain_ms": [round(t[1], 4) for t in ts],
+            "drain_kernel": drain_kernel_name(db, F.plan)}
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_1605_00930_gb300 import build as B
     B.build()
     from paper_1605_00930_gb300 import iwpp
+    if args.profile:
+        return run_profile(args)
 
     full = rank == 0 and world == 1 and not args.quick
     head_cases = load_workload(args.workload)   # generator processes start before any CUDA work
@@ -882,6 +909,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--quick", action="store_true", help="headline workload only (no other forms or operators)")
     ap.add_argument("--form-reps", type=int, default=10)
+    ap.add_argument("--profile", action="store_true",
+                    help="profiler run: the workload's batched static form only (see run_profile)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

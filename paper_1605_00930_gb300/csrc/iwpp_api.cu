@@ -434,6 +434,10 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
                       cudaStream_t stream, int phases, const LearnedCall *learned) {
     if (phases < 1 || phases > 3) return IWPP_ERR_ARG;
     if (learned && (!learned->params || !learned->order || !learned->sweeps || !learned->sws)) return IWPP_ERR_ARG;
+    if (learned) {   // the schedule the call makes is the one it queues and sweeps by
+        order = learned->order;
+        tile_sweeps = learned->sweeps;
+    }
     iwpp_plan p;
     if (plan_in) p = *plan_in; else default_batch_plan(&p);
     if (!plan_valid(p) || p.value_levels > 1) return IWPP_ERR_ARG;   // batches: one FIFO
@@ -469,10 +473,6 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
     // (cooperative 64 x 64 tiles; not the mixed-kind build), else a features pass first
     const bool fused = learned && p.local_solver == IWPP_SOLVER_COOP && k.coop.scan_feats &&
                        p.tile_h == IWPP_FEATURE_BLOCK && p.tile_w == IWPP_FEATURE_BLOCK;
-    if (learned) {
-        order = learned->order;
-        tile_sweeps = learned->sweeps;
-    }
 
     if ((phases & kPhaseScan) == 0) {   // drain only: the prepared workspace is reused
         drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);

@@ -26,12 +26,24 @@ struct CoopShared {
     unsigned long long fq[kWarpsPerCta][2];
 };
 
+#ifndef IWPP_SCAN_VEC
+#define IWPP_SCAN_VEC 0   // 1: the scan kernels copy strips with 16-byte asynchronous copies where rows allow
+#endif
+
 template <typename T, int CONN>
 __host__ __device__ constexpr size_t coop_smem_bytes() {
     return RegTile<T, CONN, kCoopStrip>::smem_per_warp(0) * kWarpsPerCta + sizeof(CoopShared);
 }
+// The scan kernels' staging area for 16-byte copies follows the drain's layout (16-byte aligned).
 template <typename T, int CONN>
-size_t coop_smem_fn(uint32_t) { return coop_smem_bytes<T, CONN>(); }
+__host__ __device__ constexpr size_t coop_scan_stage_offset() {
+    return (coop_smem_bytes<T, CONN>() + 15) & ~(size_t)15;
+}
+template <typename T, int CONN>
+size_t coop_smem_fn(uint32_t) {
+    return IWPP_SCAN_VEC ? coop_scan_stage_offset<T, CONN>() + kWarpsPerCta * RegTile<T, CONN, kCoopStrip>::kStageBytes
+                         : coop_smem_bytes<T, CONN>();
+}
 
 // Fold one strip's notification values (3 x 3 grid around the strip) into the CTA tile's:
 // the strip's top side is the tile's only for warp 0 (inside the tile otherwise, where the
@@ -251,6 +263,45 @@ __device__ __forceinline__ void strip_features(const ImageView &im, int y0, int 
     const bool u16 = RT::wide(im);
     const uint32_t M = u16 ? 0xFFFFu : 0xFFu, thr = 16u * (M / 255u);
     const int gx = x0 + 2 * lane;
+    if (y0 + TH <= im.H && x0 + 64 <= im.W) {
+        // A whole strip inside the image: both pixels of a lane's pair at once (u16x2 lanes),
+        // the same quantities as feat_pixel and the edge test below, in fewer instructions.
+        unsigned long long hist = 0;   // eight 8-bit bin counters (at most 32 pixels per lane)
+#pragma unroll
+        for (int r = 0; r < TH; r++) {
+            const uint32_t iv = I[r], jv = J[r];
+            const uint32_t dv = max2(iv, jv) - jv;   // per half max(I - J, 0): no borrow
+            const uint32_t d8 = u16 ? (dv >> 8) & 0x00FF00FFu : dv;
+            const uint32_t bl = min(7u, 32u - (uint32_t)__clz(d8 & 0xFFFFu));   // bit length, 0 for 0
+            const uint32_t bh = min(7u, 32u - (uint32_t)__clz(d8 >> 16));
+            hist += (1ull << (8 * bl)) + (1ull << (8 * bh));
+            const uint32_t x = iv ^ jv;
+            fa.seeds += (uint32_t)((x & 0xFFFFu) == 0 && (jv & 0xFFFFu) != 0) + (uint32_t)((x >> 16) == 0 && (jv >> 16) != 0);
+            fa.sI = __dp2a_lo(iv, 0x0101u, fa.sI);
+            fa.sJ = __dp2a_lo(jv, 0x0101u, fa.sJ);
+            fa.sD = __dp2a_lo(dv, 0x0101u, fa.sD);
+            if (u16) {
+                fa.sI2 += (unsigned long long)(iv & 0xFFFFu) * (iv & 0xFFFFu) + (unsigned long long)(iv >> 16) * (iv >> 16);
+                fa.sJ2 += (unsigned long long)(jv & 0xFFFFu) * (jv & 0xFFFFu) + (unsigned long long)(jv >> 16) * (jv >> 16);
+            } else {   // bytes: the squares of both pixels in one dot product
+                fa.sI2 += __dp2a_lo(iv, __byte_perm(iv, 0u, 0x0020), 0u);
+                fa.sJ2 += __dp2a_lo(jv, __byte_perm(jv, 0u, 0x0020), 0u);
+            }
+            // edges: right neighbours (column 2c + 1; 2c + 2 from the next lane, none for the
+            // tile's last column) and the pixels below (the next strip's first row for r = 15,
+            // none below the tile's last row)
+            const uint32_t rp = __byte_perm(iv, __shfl_down_sync(0xffffffffu, iv, 1), 0x5432);
+            uint32_t gxv = max2(iv, rp) - min2(iv, rp);
+            if (lane == 31) gxv &= 0xFFFFu;
+            const bool down = r + 1 < TH || (w < kWarpsPerCta - 1 && y0 + TH < im.H);
+            const uint32_t bv = r + 1 < TH ? I[r + 1 < TH ? r + 1 : r] : ib;
+            const uint32_t gyv = down ? max2(iv, bv) - min2(iv, bv) : 0u;
+            fa.edges += (uint32_t)((gxv & 0xFFFFu) + (gyv & 0xFFFFu) > thr) + (uint32_t)((gxv >> 16) + (gyv >> 16) > thr);
+        }
+        fa.h03 = (uint32_t)hist;
+        fa.h47 = (uint32_t)(hist >> 32);
+        fa.n = 2 * TH;
+    } else {
     const bool c0 = gx < im.W, c1 = gx + 1 < im.W, c2 = lane < 31 && gx + 2 < im.W;
 #pragma unroll
     for (int r = 0; r < TH; r++) {
@@ -274,11 +325,13 @@ __device__ __forceinline__ void strip_features(const ImageView &im, int y0, int 
             }
         }
     }
+    }
     uint32_t v[16];
     unsigned long long q0, q1;
     feat_reduce(fa, v, q0, q1);
-    if (lane < 16) C.fv[w][lane] = v[lane];
-    if (lane == 0) {
+    if (lane == 0) {   // static indices keep v in registers
+#pragma unroll
+        for (int k = 0; k < 16; k++) C.fv[w][k] = v[k];
         C.fq[w][0] = q0;
         C.fq[w][1] = q1;
     }
@@ -286,7 +339,7 @@ __device__ __forceinline__ void strip_features(const ImageView &im, int y0, int 
 
 template <typename T, int CONN, bool SWEEPS, bool FEATS = false>
 __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem,
-                               CoopShared &C, int w, int lane) {
+                               CoopShared &C, uint8_t *stage, int w, int lane) {
     constexpr int TH = kCoopStrip;
     using RT = RegTile<T, CONN, TH>;
     const int sweeps = !SWEEPS ? 0 : a.tile_sweeps ? (int)a.tile_sweeps[t] : a.sweeps;   // CTA-uniform
@@ -298,7 +351,13 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
     const int y0 = ty * kCoopRows + TH * w, x0 = tx * RT::TW;
     uint32_t J[TH], I[TH], jt, jb, it, ib;
+#if IWPP_SCAN_VEC
+    if (RT::vec_ok(im, x0)) RT::load_vec(im, s, stage, y0, x0, J, I, jt, jb, it, ib, lane);
+    else RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+#else
+    (void)stage;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+#endif
     if constexpr (FEATS) strip_features<RT>(im, y0, x0, J, I, ib, C, w, lane);
     bool bad = false;
 #pragma unroll
@@ -363,17 +422,18 @@ __global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : (FEATS ? 5 : 8)) scan_c
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *wsmem = smem_raw + w * RT::smem_per_warp(0);
     CoopShared &C = *reinterpret_cast<CoopShared *>(smem_raw + kWarpsPerCta * RT::smem_per_warp(0));
+    uint8_t *stage = smem_raw + coop_scan_stage_offset<T, CONN>() + w * RT::kStageBytes;
     for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const ImageView &im = image_of(a, t);
         if (!MIXED) {
-            scan_tile_coop<T, CONN, SWEEPS, FEATS>(a, im, t, wsmem, C, w, lane);
+            scan_tile_coop<T, CONN, SWEEPS, FEATS>(a, im, t, wsmem, C, stage, w, lane);
             continue;
         }
         switch (im.kind) {
-            case 0: scan_tile_coop<uint8_t, 4, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
-            case 1: scan_tile_coop<uint16_t, 4, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
-            case 2: scan_tile_coop<uint8_t, 8, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
-            default: scan_tile_coop<uint16_t, 8, SWEEPS>(a, im, t, wsmem, C, w, lane); break;
+            case 0: scan_tile_coop<uint8_t, 4, SWEEPS>(a, im, t, wsmem, C, stage, w, lane); break;
+            case 1: scan_tile_coop<uint16_t, 4, SWEEPS>(a, im, t, wsmem, C, stage, w, lane); break;
+            case 2: scan_tile_coop<uint8_t, 8, SWEEPS>(a, im, t, wsmem, C, stage, w, lane); break;
+            default: scan_tile_coop<uint16_t, 8, SWEEPS>(a, im, t, wsmem, C, stage, w, lane); break;
         }
     }
 }

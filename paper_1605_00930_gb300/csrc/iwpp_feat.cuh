@@ -47,6 +47,9 @@ __device__ __forceinline__ float block_feature(int k, const uint32_t (&v)[16], u
                                                unsigned long long sJ2, uint32_t M) {
     const uint32_t N = v[15];
     const float fN = (float)N, NM = (float)N * (float)M;
+    uint32_t vk = 0;   // v[k] without a dynamic index (which would put v in local memory)
+#pragma unroll
+    for (int q = 0; q < 16; q++) vk = q == k ? v[q] : vk;
     switch (k) {
         case 10: return (float)v[10] / NM;
         case 11: return sqrtf((float)((unsigned long long)N * sI2 - (unsigned long long)v[10] * v[10])) / NM;
@@ -54,7 +57,7 @@ __device__ __forceinline__ float block_feature(int k, const uint32_t (&v)[16], u
         case 13: return sqrtf((float)((unsigned long long)N * sJ2 - (unsigned long long)v[12] * v[12])) / NM;
         case 14: return (float)v[14] / NM;
         case 15: return log2f(fN) / 12.f;
-        default: return (float)v[k] / fN;   // histogram, seeds, edges
+        default: return (float)vk / fN;   // histogram, seeds, edges
     }
 }
 

@@ -209,6 +209,75 @@ struct RegTile {
         __syncwarp();
     }
 
+    // Bytes of the per-warp staging area of load_vec: both planes, TH rows of up to 128 bytes.
+    static constexpr int kStageBytes = 2 * TH * 128;
+
+    // Can the strip's rows be copied in 16-byte chunks? (64-column span inside the image, row
+    // pitch a multiple of 16 bytes; the planes themselves are 16-byte aligned.)
+    static __device__ __forceinline__ bool vec_ok(const ImageView &im, int x0) {
+        return x0 + TW <= im.W && ((size_t)im.W * (wide(im) ? 2 : 1)) % 16 == 0;
+    }
+
+    // load_fused with the strip's rows copied by 16-byte asynchronous copies into `stage`
+    // (global -> shared, no registers in flight): for u8 four lanes cover a 64-pixel row and
+    // one copy instruction eight rows, for u16 eight lanes a row and four rows; the lanes then
+    // read their column pairs from shared memory. Halo rows and columns as in load_fused.
+    static __device__ __forceinline__ void load_vec(const ImageView &im, const Smem &s, uint8_t *stage, int y0,
+                                                    int x0, uint32_t (&J)[TH], uint32_t (&I)[TH], uint32_t &jt,
+                                                    uint32_t &jb, uint32_t &it, uint32_t &ib, int lane) {
+        const bool w16 = wide(im);
+        const int es = w16 ? 2 : 1, cpr = 4 * es, rpl = 32 / cpr;
+        const size_t pitch = (size_t)im.W * es;
+        const int ch = lane % cpr;
+        for (int k = 0; k < TH / rpl; k++) {
+            const int rr = k * rpl + lane / cpr;
+            const size_t off = (size_t)min(y0 + rr, im.H - 1) * pitch + (size_t)x0 * es + (size_t)ch * 16;
+            const unsigned dj = static_cast<unsigned>(__cvta_generic_to_shared(stage + rr * 128 + ch * 16));
+            const unsigned di = static_cast<unsigned>(__cvta_generic_to_shared(stage + (TH + rr) * 128 + ch * 16));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dj), "l"(im.J + off) : "memory");
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(di), "l"(im.I + off) : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        const int gx = x0 + 2 * lane;
+        const uint32_t f2 = im.flip | (im.flip << 16);
+        const size_t et = (size_t)min(max(y0 - 1, 0), im.H - 1) * im.W + gx;
+        const size_t eb = (size_t)min(max(y0 + TH, 0), im.H - 1) * im.W + gx;
+        uint32_t rjt = ld_raw(im, im.J, et, true), rjb = ld_raw(im, im.J, eb, true);
+        uint32_t rit = ld_raw(im, im.I, et, false), rib = ld_raw(im, im.I, eb, false);
+        const int gy = y0 + lane - 1;
+        const bool rowin = lane < TH + 2 && gy >= 0 && gy < im.H;
+        const bool lin = rowin && x0 > 0, rin = rowin && x0 + TW < im.W;
+        const size_t hrow = (size_t)min(max(gy, 0), im.H - 1) * im.W;
+        const size_t el = hrow + max(x0 - 1, 0), er = hrow + min(x0 + TW, im.W - 1);
+        const uint32_t lj = ld1(im, im.J, el, true), rj = ld1(im, im.J, er, true);
+        const uint32_t li = ld1(im, im.I, el, false), ri = ld1(im, im.I, er, false);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < TH; r++) {
+            const bool in = y0 + r < im.H;
+            const uint32_t vj = w16 ? *reinterpret_cast<const uint32_t *>(stage + r * 128 + 4 * lane)
+                                    : unpack_raw(im, *reinterpret_cast<const uint16_t *>(stage + r * 128 + 2 * lane));
+            const uint32_t vi = w16 ? *reinterpret_cast<const uint32_t *>(stage + (TH + r) * 128 + 4 * lane)
+                                    : unpack_raw(im, *reinterpret_cast<const uint16_t *>(stage + (TH + r) * 128 +
+                                                                                          2 * lane));
+            J[r] = in ? vj ^ f2 : 0u;
+            I[r] = in ? vi ^ f2 : 0u;
+        }
+        const bool tin = y0 >= 1 && y0 - 1 < im.H, bin = y0 + TH < im.H;
+        jt = tin ? unpack_raw(im, rjt) ^ f2 : 0u;
+        it = tin ? unpack_raw(im, rit) ^ f2 : 0u;
+        jb = bin ? unpack_raw(im, rjb) ^ f2 : 0u;
+        ib = bin ? unpack_raw(im, rib) ^ f2 : 0u;
+        if (lane < TH + 2) {
+            s.hxJ[lane] = lin ? (lj ^ im.flip) << 16 : 0u;
+            s.hxJ[TH + 2 + lane] = rin ? rj ^ im.flip : 0u;
+            s.hlI[lane] = lin ? li ^ im.flip : 0u;
+            s.hrI[lane] = rin ? ri ^ im.flip : 0u;
+        }
+        __syncwarp();
+    }
+
     // Horizontal max of a packed row over (left, self, right); `h` is this lane's halo word
     // (lane 0: left halo column << 16, lane 31: right halo column, others unused).
     static __device__ __forceinline__ uint32_t hmax(uint32_t v, uint32_t h, int lane) {

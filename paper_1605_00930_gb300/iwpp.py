@@ -12,7 +12,9 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libiwpp.so")
+# The in-tree build; IWPP_LIB_PATH names another build of the same library (e.g. one compiled
+# with different tuning switches).
+LIB_PATH = os.environ.get("IWPP_LIB_PATH") or os.path.join(_HERE, "libiwpp.so")
 
 IWPP_U8, IWPP_U16 = 0, 1
 IWPP_DILATE, IWPP_ERODE = 0, 1

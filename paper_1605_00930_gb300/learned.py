@@ -117,7 +117,7 @@ class LearnedScheduler:
         self.device = device
 
     # -- training -------------------------------------------------------------------------
-    def train(self, X, T, epochs: int = 60, batch: int = 512, lr: float = 1e-3, w=(1.0, 0.25), seed: int = 1):
+    def train(self, X, T, epochs: int = 60, batch: int = 512, lr: float = 1e-3, w=(1.0, 1.0), seed: int = 1):
         import torch
         X = torch.as_tensor(X, dtype=torch.float32, device=self.device).contiguous()
         T = torch.as_tensor(T, dtype=torch.float32, device=self.device).contiguous()

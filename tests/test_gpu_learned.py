@@ -187,7 +187,21 @@ def _mixed8_cases(seed, n, side=300):
     return out
 
 
-@pytest.mark.parametrize("kind", ["mixed8", "mixed_conn", "u8"])
+def _strip_edge_cases():
+    """Heights that end a tile after one, two or three 16-row strips (whole strips at the
+    image's bottom edge) and widths that are multiples of 64, u8 and u16, both operators."""
+    out = []
+    for i, (H, W) in enumerate([(80, 128), (144, 192), (16, 64), (48, 320), (112, 64), (96, 256)]):
+        f = synth.blob_field_u8(H, W, 4, synth.rng_for(97, i))
+        mask = synth.to_u16(f) if i % 2 else f
+        if i % 3 == 2:
+            out.append(synth.Case(synth.fillholes_marker(mask), mask, 8, "erode"))
+        else:
+            out.append(synth.Case(synth.hdome_marker(mask, 3000 if i % 2 else 12), mask, 8, "dilate"))
+    return out
+
+
+@pytest.mark.parametrize("kind", ["mixed8", "mixed_conn", "u8", "strip_edges"])
 def test_learned_batch_call_bit_exact_and_features(iw, oracle_lib, kind):
     """iwpp_reconstruct_batch_learned: the schedule made inside the call (features from the scan
     kernel for one connectivity; a features pass first when connectivities are mixed) gives
@@ -197,8 +211,10 @@ def test_learned_batch_call_bit_exact_and_features(iw, oracle_lib, kind):
         cases = _mixed8_cases(41, 14)
     elif kind == "mixed_conn":
         cases = _cases(42, 10, side=300)
-    else:
+    elif kind == "u8":
         cases = [synth.tissue_case(200 + 37 * i, 150 + 53 * i, nblobs=8, image_idx=i) for i in range(5)]
+    else:
+        cases = _strip_edge_cases()
     items = _items(cases)
     sch = learned.LearnedScheduler(learned.init_params(5))
     B = iw.Batch(items)

@@ -460,28 +460,39 @@ def choose_plan(db, dev):
 
 
 def run_profile(args):
-    """A lean run for profilers: the workload's batched static form only (default plan, no
-    autotuning, no other forms), W warm-up steps then K timed steps. The persistent drain of
-    timed step k is the library's drain launch number 2 + W + k of the process (0-based: the
-    two uncaptured set-up calls come first), which is what an ncu -k / -s / -c selection needs."""
+    """A lean run for profilers: one batched form of the workload only (default plan, no
+    autotuning, no training, no other forms), W warm-up steps then K timed steps. The persistent
+    drain of timed step k is the library's drain launch number 2 + W + k of the process
+    (0-based: the two uncaptured set-up calls come first), which is what an ncu -k / -s / -c
+    selection needs. The learned form uses an untrained estimator whose sweep output is fixed
+    at 0 (as the trained one predicts on these workloads): the kernels it launches and their
+    cost do not depend on the weights otherwise."""
     import torch
     from paper_1605_00930_gb300 import build as B
     B.build()
-    from paper_1605_00930_gb300 import iwpp
+    from paper_1605_00930_gb300 import iwpp, learned
     cases = load_workload(args.workload)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     db = DeviceBatch(cases, dev)
-    F = Forms(db, None, iwpp.iwpp_default_batch_plan(), dev)
+    sch = None
+    if args.profile_form == "batched_learned":
+        p = learned.init_params(11)
+        n1 = 16 * 64 + 64 + 64 * 64 + 64          # the last layer's weights [64][2], then 2 biases
+        p[n1 + 1:n1 + 128:2] = 0.0
+        p[-1] = 0.0
+        sch = learned.LearnedScheduler(p, dev)
+    F = Forms(db, sch, iwpp.iwpp_default_batch_plan(), dev)
+    form = args.profile_form
     for _ in range(args.warmup):
         db.restore()
         flush.fill_(1)
-        F.run("batched_static", flush)
-    ts = F.timed("batched_static", flush, args.steps)
-    return {"profile_run": args.workload, "form": "batched_static", "steps": args.steps, "warmup": args.warmup,
+        F.run(form, flush)
+    ts = F.timed(form, flush, args.steps)
+    return {"profile_run": args.workload, "form": form, "steps": args.steps, "warmup": args.warmup,
             "ms": [round(t[0], 4) for t in ts], "drain_ms": [round(t[1], 4) for t in ts],
-            "drain_kernel": drain_kernel_name(db, F.plan)}
+            "drain_kernel": drain_kernel_name(db, F.plan), "launches_per_step": F.launches(form)}
 
 
 def run_ours(args, rank: int, world: int):
@@ -910,7 +921,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline workload only (no other forms or operators)")
     ap.add_argument("--form-reps", type=int, default=10)
     ap.add_argument("--profile", action="store_true",
-                    help="profiler run: the workload's batched static form only (see run_profile)")
+                    help="profiler run: one batched form of the workload only (see run_profile)")
+    ap.add_argument("--profile-form", default="batched_static", choices=["batched_static", "batched_learned"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -26,6 +26,10 @@ struct CoopShared {
     unsigned long long fq[kWarpsPerCta][2];
 };
 
+#ifndef IWPP_CHG_XOR
+#define IWPP_CHG_XOR 0   // 1: passes track "this lane changed something"; a lane that did stores all its rows
+#endif
+
 #ifndef IWPP_SCAN_VEC
 #define IWPP_SCAN_VEC 0   // 1: the scan kernels copy strips with 16-byte asynchronous copies where rows allow
 #endif
@@ -117,7 +121,7 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
         bool up_fresh = false;   // the strip's last pass was an up pass run with its current halo
         for (;;) {   // joint iterations of the strips
             if (!settled) {
-                const uint32_t chd = RT::pass_down(hx, J, I, jt, lane);
+                const uint32_t chd = RT::template pass_down<IWPP_CHG_XOR>(hx, J, I, jt, lane);
                 passes++;
                 rows |= chd;
                 // A down pass that changes nothing right after an up pass with the same halo
@@ -126,7 +130,7 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
                 if (up_fresh && !__any_sync(0xffffffffu, chd != 0)) {
                     settled = true;
                 } else {
-                    const uint32_t chu = RT::pass_up(hx, J, I, jb, lane);
+                    const uint32_t chu = RT::template pass_up<IWPP_CHG_XOR>(hx, J, I, jb, lane);
                     passes++;
                     rows |= chu;
                     // likewise an up pass that changes nothing after a down pass with the same
@@ -153,6 +157,11 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
         if (w == 0 && lane == 0) st.visits++;
         IWPP_CO_MARK(1);
         if (__syncthreads_or(rows != 0)) {
+#if IWPP_CHG_XOR
+            // a lane that changed a pixel writes all its rows inside the image
+            const int nin = im.H - y0;
+            rows = rows == 0 || nin <= 0 ? 0u : (nin >= TH ? 0xFFFFu : (1u << nin) - 1u);
+#endif
             RT::store(im, y0, x0, J, rows, lane);
             RT::notify_scan(s, J, jt, jb, it, ib, lane);
             if (lane == 0) coop_fold_misc(C, s.misc, w);
@@ -415,8 +424,11 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
 // SWEEPS: the build that runs sweep pairs (plans with sweeps, per-tile sweep counts); the
 // other one only checks and collects the frontier, with few enough registers for 8 CTAs per
 // SM (the scan is a pass over every pixel: loads in flight are what it needs).
+#ifndef IWPP_SCAN_FEATS_MINB
+#define IWPP_SCAN_FEATS_MINB 5   // CTAs per SM the scan build with features is compiled for
+#endif
 template <typename T, int CONN, bool MIXED, bool SWEEPS, bool FEATS = false>
-__global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : (FEATS ? 5 : 8)) scan_coop_kernel(EngineArgs a) {
+__global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : (FEATS ? IWPP_SCAN_FEATS_MINB : 8)) scan_coop_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;

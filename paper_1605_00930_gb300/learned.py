@@ -9,7 +9,8 @@ this module only drives it through the C ABI:
     per-tile work counters on; per 64 x 64 block the work label is log(1 + SM cycles spent
     on the block's tiles) in the run with the plan's own sweep count, and the sweep label
     is the smallest s that no larger option beats by more than SWEEP_MARGIN (cycle counts
-    of single runs are noisy; extra sweeps must pay for themselves clearly);
+    of single runs are noisy; extra sweeps must pay for themselves clearly); the estimator's
+    sweep output learns whether that label is above 0;
   * training runs the library's hand-written FP32 backpropagation and Adam kernels;
   * weights are saved as raw float32 plus a JSON header; a missing or corrupt file
     means the static schedule is used.
@@ -194,17 +195,22 @@ class LearnedScheduler:
 
 
 def train_from_workloads(item_sets, n_samples: int = 50000, epochs: int = 60, seed: int = 7, plan=None,
-                         device="cuda"):
-    """Generate labels from runs of each batch in `item_sets`, sample n_samples blocks and
-    train a scheduler. Returns (scheduler, report)."""
-    Xs, T0s, T1s = [], [], []
+                         device="cuda", reps: int = 2):
+    """Generate labels from runs of each batch in `item_sets` (cycles averaged over `reps`
+    runs per sweep option), sample n_samples blocks and train a scheduler. The sweep output is
+    trained on "do sweeps pay here" (1 if the block's sweep label is > 0, else 0), so that the
+    schedule runs one sweep pair where the estimator expects it to pay and none elsewhere.
+    Returns (scheduler, report)."""
+    Xs, T0s, T1s, Ls = [], [], [], []
     for items in item_sets:
         Xs.append(features(items, device).cpu().numpy())
-        lw, best, _ = block_labels(items, plan)
+        lw, best, _ = block_labels(items, plan, reps=reps)
         T0s.append(lw)
-        T1s.append(best)
+        T1s.append((best > 0).astype(np.float64))
+        Ls.append(best)
     X = np.concatenate(Xs)
     T = np.stack([np.concatenate(T0s), np.concatenate(T1s)], axis=1)
+    labels = np.concatenate(Ls)
     rng = np.random.default_rng(seed)
     idx = rng.permutation(X.shape[0])[:min(n_samples, X.shape[0])]
     ntr = int(len(idx) * 0.9)
@@ -219,7 +225,8 @@ def train_from_workloads(item_sets, n_samples: int = 50000, epochs: int = 60, se
         "mae_logwork_const": float(np.mean(np.abs(base[0] - T[te, 0]))),
         "mae_sweeps": float(np.mean(np.abs(np.clip(np.rint(pred[:, 1]), 0, 8) - T[te, 1]))),
         "mae_sweeps_const": float(np.mean(np.abs(np.rint(base[1]) - T[te, 1]))),
-        "sweep_label_share": {str(o): round(float(np.mean(T[:, 1] == o)), 4) for o in SWEEP_OPTIONS},
+        "sweeps_predicted_share": round(float(np.mean(np.rint(pred[:, 1]) >= 1)), 4),
+        "sweep_label_share": {str(o): round(float(np.mean(labels == o)), 4) for o in SWEEP_OPTIONS},
     }
     sch.meta.update({"report": report})
     return sch, report

@@ -460,13 +460,14 @@ def choose_plan(db, dev):
 
 
 def run_profile(args):
-    """A lean run for profilers: one batched form of the workload only (default plan, no
-    autotuning, no training, no other forms), W warm-up steps then K timed steps. The persistent
-    drain of timed step k is the library's drain launch number 2 + W + k of the process
-    (0-based: the two uncaptured set-up calls come first), which is what an ncu -k / -s / -c
-    selection needs. The learned form uses an untrained estimator whose sweep output is fixed
-    at 0 (as the trained one predicts on these workloads): the kernels it launches and their
-    cost do not depend on the weights otherwise."""
+    """A lean run for profilers: one form of the workload only (default plan, no autotuning,
+    no training, no other forms), W warm-up steps then K timed steps. A batched form's
+    persistent drain of timed step k is the library's drain launch number 2 + W + k of the
+    process (0-based: two uncaptured batch set-up calls come first); the plain form launches
+    one drain per image and step after those two. That is what an ncu -k / -s / -c selection
+    needs. The learned form uses an untrained estimator whose sweep output is fixed at 0 (as
+    the trained one predicts on these workloads): the kernels it launches and their cost do
+    not depend on the weights otherwise."""
     import torch
     from paper_1605_00930_gb300 import build as B
     B.build()
@@ -922,7 +923,7 @@ def main():
     ap.add_argument("--form-reps", type=int, default=10)
     ap.add_argument("--profile", action="store_true",
                     help="profiler run: one batched form of the workload only (see run_profile)")
-    ap.add_argument("--profile-form", default="batched_static", choices=["batched_static", "batched_learned"])
+    ap.add_argument("--profile-form", default="batched_static", choices=["batched_static", "batched_learned", "plain"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -27,7 +27,7 @@ struct CoopShared {
 };
 
 #ifndef IWPP_CHG_XOR
-#define IWPP_CHG_XOR 0   // 1: passes track "this lane changed something"; a lane that did stores all its rows
+#define IWPP_CHG_XOR 1   // 1: passes track "this lane changed something"; a lane that did stores all its rows
 #endif
 
 #ifndef IWPP_SCAN_VEC
@@ -421,11 +421,77 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     __syncthreads();   // the strips' shared halo buffers are reloaded for the next tile
 }
 
-// SWEEPS: the build that runs sweep pairs (plans with sweeps, per-tile sweep counts); the
-// other one only checks and collects the frontier, with few enough registers for 8 CTAs per
-// SM (the scan is a pass over every pixel: loads in flight are what it needs).
+// The lean scan (no sweeps, no features), one warp per strip with no CTA barriers: each warp
+// loads a 16-row strip of a tile with its halo, checks the precondition and whether one of
+// its pixels can rise; a strip that can makes its tile PENDING (batches: a fire-and-forget
+// OR) or notifies it (single images: the first notification queues the tile, later ones
+// find it PENDING). Warps go from strip to strip independently, 8 CTAs per SM: the scan is a
+// pass over every pixel, and loads in flight are what it needs.
+#ifndef IWPP_SCAN_STRIP_MINB
+#define IWPP_SCAN_STRIP_MINB 7   // CTAs per SM of the strip scan (72 registers, no spills)
+#endif
+#ifndef IWPP_SCAN_STRIPS
+#define IWPP_SCAN_STRIPS 1       // 0: the lean scan works on whole tiles with CTA barriers (measured)
+#endif
+
+template <typename T, int CONN>
+__device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32_t t, int sw, uint8_t *wsmem,
+                                int lane) {
+    constexpr int TH = kCoopStrip;
+    using RT = RegTile<T, CONN, TH>;
+    const uint32_t lt = t - im.tile_base;
+    const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
+    const int y0 = ty * kCoopRows + TH * sw, x0 = tx * RT::TW;
+    if (y0 >= im.H) return;   // a strip below the image (warp-uniform): nothing in it can rise
+    const long long c0 = clock64();
+    const typename RT::Smem s = RT::carve(wsmem);
+    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    uint32_t J[TH], I[TH], jt, jb, it, ib;
+    RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
+    const bool can = RT::improvable(hx, J, I, jt, jb, lane);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        if (can) {
+            if (a.defer_push) mark_pending(a, t); else notify_tile(a, t);
+        }
+        if (bad) set_status(a.hdr, kErrPrecondition);
+        if (a.tile_work) atomicAdd(a.tile_work + a.ntiles + t, (uint32_t)min(clock64() - c0, 0x7fffffffll));
+    }
+    __syncwarp();   // the warp's halo buffers are reloaded for its next strip
+}
+
+template <typename T, int CONN, bool MIXED>
+__global__ void __launch_bounds__(kThreads, IWPP_SCAN_STRIP_MINB) scan_strip_coop_kernel(EngineArgs a) {
+    using RT = RegTile<T, CONN, kCoopStrip>;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *wsmem = smem_raw + w * RT::smem_per_warp(0);
+    const uint64_t nunits = (uint64_t)a.ntiles * kWarpsPerCta, nwarps = (uint64_t)gridDim.x * kWarpsPerCta;
+    for (uint64_t u = (uint64_t)blockIdx.x * kWarpsPerCta + w; u < nunits; u += nwarps) {
+        const uint32_t t = (uint32_t)(u / kWarpsPerCta);
+        const int sw = (int)(u % kWarpsPerCta);
+        const ImageView &im = image_of(a, t);
+        if (!MIXED) {
+            scan_strip_coop<T, CONN>(a, im, t, sw, wsmem, lane);
+            continue;
+        }
+        switch (im.kind) {
+            case 0: scan_strip_coop<uint8_t, 4>(a, im, t, sw, wsmem, lane); break;
+            case 1: scan_strip_coop<uint16_t, 4>(a, im, t, sw, wsmem, lane); break;
+            case 2: scan_strip_coop<uint8_t, 8>(a, im, t, sw, wsmem, lane); break;
+            default: scan_strip_coop<uint16_t, 8>(a, im, t, sw, wsmem, lane); break;
+        }
+    }
+}
+
+// SWEEPS: the build that runs sweep pairs (plans with sweeps, per-tile sweep counts); FEATS:
+// the build that also writes the tile's features. Both work on whole tiles (the sweeps
+// exchange boundary rows between the strips, the features sum over the strips).
 #ifndef IWPP_SCAN_FEATS_MINB
-#define IWPP_SCAN_FEATS_MINB 5   // CTAs per SM the scan build with features is compiled for
+#define IWPP_SCAN_FEATS_MINB 6   // CTAs per SM the scan build with features is compiled for (measured: 5, 6, 7)
 #endif
 template <typename T, int CONN, bool MIXED, bool SWEEPS, bool FEATS = false>
 __global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : (FEATS ? IWPP_SCAN_FEATS_MINB : 8)) scan_coop_kernel(EngineArgs a) {

@@ -899,10 +899,12 @@ struct Tile {
 
 // ---- per-tile bodies shared by the single-image and the batch kernels -------------------------
 
-// Mark tile t PENDING without queueing it (the compact kernel queues it later, in order).
-__device__ inline void mark_pending(const EngineArgs &a, uint32_t t) {
-    const uint32_t old = atomicOr(a.state + t, ST_PENDING);
-    if ((old & (ST_PENDING | ST_ACTIVE)) == 0) atomicAdd(&a.hdr->pending, 1u);
+// Mark tile t PENDING without queueing it (batches: the compact kernel queues it later, in
+// order, and the finalize kernel counts the PENDING tiles into the pending count). Nothing
+// else changes a state word before the persistent kernel starts, so the OR needs no result:
+// a fire-and-forget reduction, no round trip.
+__device__ __forceinline__ void mark_pending(const EngineArgs &a, uint32_t t) {
+    atomicOr(a.state + t, ST_PENDING);
 }
 
 // Tile-parallel scan of one tile (the frontier-initialisation kernel's body):
@@ -1203,15 +1205,19 @@ static __global__ void __launch_bounds__(256) finalize_queue_kernel(EngineArgs a
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t nround = (a.ntiles + 31) / 32 * 32;
+    uint32_t npending = 0;   // lane 0: PENDING tiles of this warp's rounds (every one is queued)
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
-        bool want = false;
+        bool want = false, pend = false;
         if (t < a.ntiles) {
             const uint32_t s = a.state[t];
-            want = (s & ST_PENDING) != 0 && (s & ST_QUEUED) == 0;
+            pend = (s & ST_PENDING) != 0;
+            want = pend && (s & ST_QUEUED) == 0;
             if (s & ST_QUEUED) a.state[t] = s & ~ST_QUEUED;
         }
+        npending += (uint32_t)__popc(__ballot_sync(0xffffffffu, pend));
         queue_warp(a, want, t, lane);
     }
+    if (lane == 0 && npending) atomicAdd(&a.hdr->pending, npending);
 }
 
 // Write a chunk of the batch's image table into the workspace (descriptors travel as

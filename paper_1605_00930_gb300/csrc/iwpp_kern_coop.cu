@@ -8,7 +8,11 @@ namespace iwpp {
 template <typename T, int CONN, bool MIXED = false>
 static RegKernelSet coop_set() {
     RegKernelSet k;
+#if IWPP_SCAN_STRIPS
+    k.scan = scan_strip_coop_kernel<T, CONN, MIXED>;
+#else
     k.scan = scan_coop_kernel<T, CONN, MIXED, false>;
+#endif
     k.drain = drain_coop_kernel<T, CONN, MIXED>;
     k.drain_hi = nullptr;   // one build of the persistent kernel
     k.smem = &coop_smem_fn<T, CONN>;

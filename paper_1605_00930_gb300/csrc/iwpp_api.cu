@@ -269,6 +269,7 @@ static void fill_common(EngineArgs &a, const iwpp_plan &p, uint8_t *base, size_t
     a.lvl = nullptr;
     a.tile_img = nullptr;
     a.feats = nullptr;
+    a.fsums = nullptr;
     a.sweep_only = 0;
 }
 
@@ -506,16 +507,23 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
         if (rc != IWPP_OK) return rc;
     }
     if (fused) {
-        // scan with features (no sweeps yet) -> MLP and order -> sweeps-only pass
-        a.feats = sched_features(imgs, n, p, learned->sws, learned->sws_bytes);
-        if (!a.feats) return IWPP_ERR_WORKSPACE;
+        // scan whose strips add up their tile's feature sums (no sweeps yet) -> features ->
+        // MLP and order -> sweeps-only pass
+        float *feats = sched_features(imgs, n, p, learned->sws, learned->sws_bytes);
+        size_t fbytes = 0;
+        FeatSums *fs = sched_feature_sums(imgs, n, p, learned->sws, learned->sws_bytes, &fbytes);
+        if (!feats || !fs) return IWPP_ERR_WORKSPACE;
+        if (cudaMemsetAsync(fs, 0, fbytes, stream) != cudaSuccess) return IWPP_ERR_CUDA;
+        a.fsums = fs;
         a.tile_sweeps = nullptr;
         k.coop.scan_feats<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
         if (cudaGetLastError() != cudaSuccess) return IWPP_ERR_CUDA;
-        const int rc = schedule_batch(imgs, n, p, learned->params, learned->order, learned->sweeps, learned->sws,
-                                      learned->sws_bytes, stream, 6);
+        a.fsums = nullptr;
+        int rc = features_from_sums(fs, L.ntiles, feats, stream);
         if (rc != IWPP_OK) return rc;
-        a.feats = nullptr;
+        rc = schedule_batch(imgs, n, p, learned->params, learned->order, learned->sweeps, learned->sws,
+                            learned->sws_bytes, stream, 6);
+        if (rc != IWPP_OK) return rc;
         a.tile_sweeps = learned->sweeps;
         a.sweep_only = 1;
         k.coop.scan_sweeps<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
@@ -536,7 +544,7 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
 int batch_launches(int n, int phases) {
     const int chunks = (n + kDescChunk - 1) / kDescChunk;
     int prep = chunks + 4;   // table chunks, tile map, scan, compact, finalize
-    if (phases & 4) prep += chunks + 5;
+    if (phases & 4) prep += chunks + 6;   // schedule table chunks, features, MLP, keys, scan, scatter, sweeps
     return ((phases & kPhaseScan) ? prep : 0) + ((phases & kPhaseDrain) ? 1 : 0);
 }
 

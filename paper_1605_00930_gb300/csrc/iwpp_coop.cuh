@@ -22,8 +22,6 @@ struct CoopShared {
     uint32_t rows[kWarpsPerCta][2][32];   // each strip's first and last row, per lane
     uint32_t misc[16];                    // the CTA tile's notification values (3 x 3 grid)
     uint32_t tile, redo;
-    uint32_t fv[kWarpsPerCta][16];        // scan with features: each strip's feature sums
-    unsigned long long fq[kWarpsPerCta][2];
 };
 
 #ifndef IWPP_CHG_XOR
@@ -255,18 +253,15 @@ __global__ void __launch_bounds__(kThreads, MIXED ? kRegBlocks : kCoopBlocks) dr
 #endif
 }
 
-// Initialisation of one CTA tile (Algorithm 7's scanning phase, tile-local, then the
-// frontier): check the precondition; run the tile's raster / anti-raster sweep pairs
-// (a.tile_sweeps[t], else a.sweeps), the strips exchanging their boundary rows after each
-// pair, store what changed and notify the neighbours whose halo pixels the tile can now
-// raise; queue the tile if one of its pixels can still rise.
-// Feature sums of one strip (iwpp_feat.cuh) into C.fv[w] / C.fq[w]: every pixel of the strip
-// inside the image, with its right neighbour (in the tile) and the one below (the next strip's
-// first row is the halo row `ib`; below the tile's last row there is none).
+// Feature sums of one strip (iwpp_feat.cuh) into v / q0 / q1 (every lane ends with them):
+// every pixel of the strip inside the image, with its right neighbour (in the tile) and the
+// one below (the next strip's first row is the halo row `ib`; below the tile's last row there
+// is none).
 template <typename RT>
-__device__ __forceinline__ void strip_features(const ImageView &im, int y0, int x0, const uint32_t (&J)[RT::kRows],
-                                               const uint32_t (&I)[RT::kRows], uint32_t ib, CoopShared &C, int w,
-                                               int lane) {
+__device__ __forceinline__ void strip_feature_sums(const ImageView &im, int y0, int x0,
+                                                   const uint32_t (&J)[RT::kRows], const uint32_t (&I)[RT::kRows],
+                                                   uint32_t ib, int w, int lane, uint32_t (&v)[16],
+                                                   unsigned long long &q0, unsigned long long &q1) {
     constexpr int TH = RT::kRows;
     FeatAcc fa;
     const bool u16 = RT::wide(im);
@@ -335,18 +330,33 @@ __device__ __forceinline__ void strip_features(const ImageView &im, int y0, int 
         }
     }
     }
-    uint32_t v[16];
-    unsigned long long q0, q1;
     feat_reduce(fa, v, q0, q1);
-    if (lane == 0) {   // static indices keep v in registers
-#pragma unroll
-        for (int k = 0; k < 16; k++) C.fv[w][k] = v[k];
-        C.fq[w][0] = q0;
-        C.fq[w][1] = q1;
-    }
 }
 
-template <typename T, int CONN, bool SWEEPS, bool FEATS = false>
+// A strip's feature sums added into its tile's FeatSums (fire-and-forget reductions; the
+// first strip also records MAXV in v[11]).
+template <typename RT>
+__device__ __forceinline__ void strip_features_add(const ImageView &im, int y0, int x0,
+                                                   const uint32_t (&J)[RT::kRows], const uint32_t (&I)[RT::kRows],
+                                                   uint32_t ib, FeatSums *fs, int w, int lane) {
+    uint32_t v[16];
+    unsigned long long q0, q1;
+    strip_feature_sums<RT>(im, y0, x0, J, I, ib, w, lane, v, q0, q1);
+    if (w == 0) v[11] = RT::wide(im) ? 0xFFFFu : 0xFFu;
+    uint32_t mine = 0;   // lane k < 16: v[k], selected without a dynamic index
+#pragma unroll
+    for (int k = 0; k < 16; k++) mine = k == lane ? v[k] : mine;
+    if (lane < 16 && mine) atomicAdd(&fs->v[lane], mine);
+    if (lane == 16) atomicAdd(&fs->q[0], q0);
+    if (lane == 17) atomicAdd(&fs->q[1], q1);
+}
+
+// Initialisation of one CTA tile (Algorithm 7's scanning phase, tile-local, then the
+// frontier): check the precondition; run the tile's raster / anti-raster sweep pairs
+// (a.tile_sweeps[t], else a.sweeps), the strips exchanging their boundary rows after each
+// pair, store what changed and notify the neighbours whose halo pixels the tile can now
+// raise; queue the tile if one of its pixels can still rise.
+template <typename T, int CONN, bool SWEEPS>
 __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem,
                                CoopShared &C, uint8_t *stage, int w, int lane) {
     constexpr int TH = kCoopStrip;
@@ -367,7 +377,6 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     (void)stage;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
 #endif
-    if constexpr (FEATS) strip_features<RT>(im, y0, x0, J, I, ib, C, w, lane);
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
@@ -385,16 +394,6 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     const bool can = RT::improvable(hx, J, I, jt, jb, lane);
     const int any_bad = __syncthreads_or(bad);
     const int any_can = __syncthreads_or(can);
-    if constexpr (FEATS) {   // the strips' sums are in C.fv / C.fq (barriers above)
-        if (w == 0 && lane < 16) {
-            uint32_t v[16];
-#pragma unroll
-            for (int k = 0; k < 16; k++) v[k] = C.fv[0][k] + C.fv[1][k] + C.fv[2][k] + C.fv[3][k];
-            const unsigned long long q0 = C.fq[0][0] + C.fq[1][0] + C.fq[2][0] + C.fq[3][0];
-            const unsigned long long q1 = C.fq[0][1] + C.fq[1][1] + C.fq[2][1] + C.fq[3][1];
-            a.feats[(size_t)t * 16 + lane] = block_feature(lane, v, q0, q1, RT::wide(im) ? 0xFFFFu : 0xFFu);
-        }
-    }
     if (sweeps > 0 && __syncthreads_or(rows != 0)) {
         RT::store(im, y0, x0, J, rows, lane);
         if (threadIdx.x < 16) C.misc[threadIdx.x] = 0;
@@ -425,8 +424,12 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
 // loads a 16-row strip of a tile with its halo, checks the precondition and whether one of
 // its pixels can rise; a strip that can makes its tile PENDING (batches: a fire-and-forget
 // OR) or notifies it (single images: the first notification queues the tile, later ones
-// find it PENDING). Warps go from strip to strip independently, 8 CTAs per SM: the scan is a
-// pass over every pixel, and loads in flight are what it needs.
+// find it PENDING). Warps go from strip to strip independently, 7 CTAs per SM: the scan is a
+// pass over every pixel, and loads in flight are what it needs. FEATS: each strip also adds
+// its pixels' feature sums into its tile's FeatSums (learned batches).
+#ifndef IWPP_SCAN_FEATS_MINB
+#define IWPP_SCAN_FEATS_MINB 5   // CTAs per SM of the strip scan with features (96 registers)
+#endif
 #ifndef IWPP_SCAN_STRIP_MINB
 #define IWPP_SCAN_STRIP_MINB 7   // CTAs per SM of the strip scan (72 registers, no spills)
 #endif
@@ -434,7 +437,7 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
 #define IWPP_SCAN_STRIPS 1       // 0: the lean scan works on whole tiles with CTA barriers (measured)
 #endif
 
-template <typename T, int CONN>
+template <typename T, int CONN, bool FEATS = false>
 __device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32_t t, int sw, uint8_t *wsmem,
                                 int lane) {
     constexpr int TH = kCoopStrip;
@@ -448,6 +451,7 @@ __device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32
     const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
     uint32_t J[TH], I[TH], jt, jb, it, ib;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
+    if constexpr (FEATS) strip_features_add<RT>(im, y0, x0, J, I, ib, static_cast<FeatSums *>(a.fsums) + t, sw, lane);
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
@@ -463,8 +467,9 @@ __device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32
     __syncwarp();   // the warp's halo buffers are reloaded for its next strip
 }
 
-template <typename T, int CONN, bool MIXED>
-__global__ void __launch_bounds__(kThreads, IWPP_SCAN_STRIP_MINB) scan_strip_coop_kernel(EngineArgs a) {
+template <typename T, int CONN, bool MIXED, bool FEATS = false>
+__global__ void __launch_bounds__(kThreads, FEATS ? IWPP_SCAN_FEATS_MINB : IWPP_SCAN_STRIP_MINB)
+    scan_strip_coop_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, IWPP_SCAN_STRIP_MINB) scan_strip_coo
         const int sw = (int)(u % kWarpsPerCta);
         const ImageView &im = image_of(a, t);
         if (!MIXED) {
-            scan_strip_coop<T, CONN>(a, im, t, sw, wsmem, lane);
+            scan_strip_coop<T, CONN, FEATS>(a, im, t, sw, wsmem, lane);
             continue;
         }
         switch (im.kind) {
@@ -487,14 +492,11 @@ __global__ void __launch_bounds__(kThreads, IWPP_SCAN_STRIP_MINB) scan_strip_coo
     }
 }
 
-// SWEEPS: the build that runs sweep pairs (plans with sweeps, per-tile sweep counts); FEATS:
-// the build that also writes the tile's features. Both work on whole tiles (the sweeps
-// exchange boundary rows between the strips, the features sum over the strips).
-#ifndef IWPP_SCAN_FEATS_MINB
-#define IWPP_SCAN_FEATS_MINB 6   // CTAs per SM the scan build with features is compiled for (measured: 5, 6, 7)
-#endif
-template <typename T, int CONN, bool MIXED, bool SWEEPS, bool FEATS = false>
-__global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : (FEATS ? IWPP_SCAN_FEATS_MINB : 8)) scan_coop_kernel(EngineArgs a) {
+// The scan on whole tiles: SWEEPS, the build that runs sweep pairs (plans with sweeps,
+// per-tile sweep counts; the strips exchange boundary rows after each pair); the other one
+// is the lean scan with CTA barriers (the strip scan above replaces it).
+template <typename T, int CONN, bool MIXED, bool SWEEPS>
+__global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : 8) scan_coop_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : (FEATS ? IWPP_SCAN_FEAT
     for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const ImageView &im = image_of(a, t);
         if (!MIXED) {
-            scan_tile_coop<T, CONN, SWEEPS, FEATS>(a, im, t, wsmem, C, stage, w, lane);
+            scan_tile_coop<T, CONN, SWEEPS>(a, im, t, wsmem, C, stage, w, lane);
             continue;
         }
         switch (im.kind) {

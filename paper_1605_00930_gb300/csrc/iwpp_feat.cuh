@@ -61,6 +61,13 @@ __device__ __forceinline__ float block_feature(int k, const uint32_t (&v)[16], u
     }
 }
 
+// A block's sums, added up by the strips that make it (v as above, v[11] = MAXV; q = sums of
+// squares of I and J).
+struct FeatSums {
+    uint32_t v[16];
+    unsigned long long q[2];
+};
+
 // Warp-wide sums of each lane's FeatAcc into v / sI2 / sJ2 (every lane ends with them).
 __device__ __forceinline__ void feat_reduce(const FeatAcc &a, uint32_t (&v)[16], unsigned long long &sI2,
                                             unsigned long long &sJ2) {

@@ -19,7 +19,7 @@ static RegKernelSet coop_set() {
     k.scan_sweeps = scan_coop_kernel<T, CONN, MIXED, true>;
     // features in the scan: not for the mixed-kind build (its scan would inline four copies)
     if constexpr (MIXED) k.scan_feats = nullptr;
-    else k.scan_feats = scan_coop_kernel<T, CONN, false, false, true>;
+    else k.scan_feats = scan_strip_coop_kernel<T, CONN, false, true>;
     return k;
 }
 

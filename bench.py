@@ -154,9 +154,10 @@ def _traffic_from_profiles(kernel: str, workload: str):
     if not os.path.exists(path):
         return None
     digest = kernel_digest()
+    name = kernel.replace(" ", "")   # records name the kernel without spaces
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == digest:
+        if len(parts) >= 4 and parts[0] == name and parts[1] == workload and parts[2] == digest:
             return float(parts[3])
     return None
 

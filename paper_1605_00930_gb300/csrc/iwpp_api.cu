@@ -269,7 +269,6 @@ static void fill_common(EngineArgs &a, const iwpp_plan &p, uint8_t *base, size_t
     a.lvl = nullptr;
     a.tile_img = nullptr;
     a.feats = nullptr;
-    a.fsums = nullptr;
     a.sweep_only = 0;
 }
 
@@ -507,21 +506,16 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
         if (rc != IWPP_OK) return rc;
     }
     if (fused) {
-        // scan whose strips add up their tile's feature sums (no sweeps yet) -> features ->
-        // MLP and order -> sweeps-only pass
+        // scan that also writes every tile's features (no sweeps yet) -> MLP and order ->
+        // sweeps-only pass
         float *feats = sched_features(imgs, n, p, learned->sws, learned->sws_bytes);
-        size_t fbytes = 0;
-        FeatSums *fs = sched_feature_sums(imgs, n, p, learned->sws, learned->sws_bytes, &fbytes);
-        if (!feats || !fs) return IWPP_ERR_WORKSPACE;
-        if (cudaMemsetAsync(fs, 0, fbytes, stream) != cudaSuccess) return IWPP_ERR_CUDA;
-        a.fsums = fs;
+        if (!feats) return IWPP_ERR_WORKSPACE;
+        a.feats = feats;
         a.tile_sweeps = nullptr;
         k.coop.scan_feats<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
         if (cudaGetLastError() != cudaSuccess) return IWPP_ERR_CUDA;
-        a.fsums = nullptr;
-        int rc = features_from_sums(fs, L.ntiles, feats, stream);
-        if (rc != IWPP_OK) return rc;
-        rc = schedule_batch(imgs, n, p, learned->params, learned->order, learned->sweeps, learned->sws,
+        a.feats = nullptr;
+        int rc = schedule_batch(imgs, n, p, learned->params, learned->order, learned->sweeps, learned->sws,
                             learned->sws_bytes, stream, 6);
         if (rc != IWPP_OK) return rc;
         a.tile_sweeps = learned->sweeps;
@@ -544,7 +538,7 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
 int batch_launches(int n, int phases) {
     const int chunks = (n + kDescChunk - 1) / kDescChunk;
     int prep = chunks + 4;   // table chunks, tile map, scan, compact, finalize
-    if (phases & 4) prep += chunks + 6;   // schedule table chunks, features, MLP, keys, scan, scatter, sweeps
+    if (phases & 4) prep += chunks + 5;   // schedule table chunks, MLP, keys, bucket scan, scatter, sweeps
     return ((phases & kPhaseScan) ? prep : 0) + ((phases & kPhaseDrain) ? 1 : 0);
 }
 

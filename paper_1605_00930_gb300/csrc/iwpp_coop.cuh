@@ -10,7 +10,6 @@
 // images and uniform batches; the mixed build dispatches on each tile's image kind.
 #pragma once
 
-#include "iwpp_feat.cuh"
 #include "iwpp_regtile.cuh"
 
 namespace iwpp {
@@ -253,104 +252,6 @@ __global__ void __launch_bounds__(kThreads, MIXED ? kRegBlocks : kCoopBlocks) dr
 #endif
 }
 
-// Feature sums of one strip (iwpp_feat.cuh) into v / q0 / q1 (every lane ends with them):
-// every pixel of the strip inside the image, with its right neighbour (in the tile) and the
-// one below (the next strip's first row is the halo row `ib`; below the tile's last row there
-// is none).
-template <typename RT>
-__device__ __forceinline__ void strip_feature_sums(const ImageView &im, int y0, int x0,
-                                                   const uint32_t (&J)[RT::kRows], const uint32_t (&I)[RT::kRows],
-                                                   uint32_t ib, int w, int lane, uint32_t (&v)[16],
-                                                   unsigned long long &q0, unsigned long long &q1) {
-    constexpr int TH = RT::kRows;
-    FeatAcc fa;
-    const bool u16 = RT::wide(im);
-    const uint32_t M = u16 ? 0xFFFFu : 0xFFu, thr = 16u * (M / 255u);
-    const int gx = x0 + 2 * lane;
-    if (y0 + TH <= im.H && x0 + 64 <= im.W) {
-        // A whole strip inside the image: both pixels of a lane's pair at once (u16x2 lanes),
-        // the same quantities as feat_pixel and the edge test below, in fewer instructions.
-        unsigned long long hist = 0;   // eight 8-bit bin counters (at most 32 pixels per lane)
-#pragma unroll
-        for (int r = 0; r < TH; r++) {
-            const uint32_t iv = I[r], jv = J[r];
-            const uint32_t dv = max2(iv, jv) - jv;   // per half max(I - J, 0): no borrow
-            const uint32_t d8 = u16 ? (dv >> 8) & 0x00FF00FFu : dv;
-            const uint32_t bl = min(7u, 32u - (uint32_t)__clz(d8 & 0xFFFFu));   // bit length, 0 for 0
-            const uint32_t bh = min(7u, 32u - (uint32_t)__clz(d8 >> 16));
-            hist += (1ull << (8 * bl)) + (1ull << (8 * bh));
-            const uint32_t x = iv ^ jv;
-            fa.seeds += (uint32_t)((x & 0xFFFFu) == 0 && (jv & 0xFFFFu) != 0) + (uint32_t)((x >> 16) == 0 && (jv >> 16) != 0);
-            fa.sI = __dp2a_lo(iv, 0x0101u, fa.sI);
-            fa.sJ = __dp2a_lo(jv, 0x0101u, fa.sJ);
-            fa.sD = __dp2a_lo(dv, 0x0101u, fa.sD);
-            if (u16) {
-                fa.sI2 += (unsigned long long)(iv & 0xFFFFu) * (iv & 0xFFFFu) + (unsigned long long)(iv >> 16) * (iv >> 16);
-                fa.sJ2 += (unsigned long long)(jv & 0xFFFFu) * (jv & 0xFFFFu) + (unsigned long long)(jv >> 16) * (jv >> 16);
-            } else {   // bytes: the squares of both pixels in one dot product
-                fa.sI2 += __dp2a_lo(iv, __byte_perm(iv, 0u, 0x0020), 0u);
-                fa.sJ2 += __dp2a_lo(jv, __byte_perm(jv, 0u, 0x0020), 0u);
-            }
-            // edges: right neighbours (column 2c + 1; 2c + 2 from the next lane, none for the
-            // tile's last column) and the pixels below (the next strip's first row for r = 15,
-            // none below the tile's last row)
-            const uint32_t rp = __byte_perm(iv, __shfl_down_sync(0xffffffffu, iv, 1), 0x5432);
-            uint32_t gxv = max2(iv, rp) - min2(iv, rp);
-            if (lane == 31) gxv &= 0xFFFFu;
-            const bool down = r + 1 < TH || (w < kWarpsPerCta - 1 && y0 + TH < im.H);
-            const uint32_t bv = r + 1 < TH ? I[r + 1 < TH ? r + 1 : r] : ib;
-            const uint32_t gyv = down ? max2(iv, bv) - min2(iv, bv) : 0u;
-            fa.edges += (uint32_t)((gxv & 0xFFFFu) + (gyv & 0xFFFFu) > thr) + (uint32_t)((gxv >> 16) + (gyv >> 16) > thr);
-        }
-        fa.h03 = (uint32_t)hist;
-        fa.h47 = (uint32_t)(hist >> 32);
-        fa.n = 2 * TH;
-    } else {
-    const bool c0 = gx < im.W, c1 = gx + 1 < im.W, c2 = lane < 31 && gx + 2 < im.W;
-#pragma unroll
-    for (int r = 0; r < TH; r++) {
-        if (y0 + r < im.H) {   // warp-uniform
-            const uint32_t iv = I[r], jv = J[r];
-            const uint32_t nxt = __shfl_down_sync(0xffffffffu, iv, 1);
-            const bool down = y0 + r + 1 < im.H && (r + 1 < TH || w < kWarpsPerCta - 1);
-            const uint32_t bv = r + 1 < TH ? I[r + 1 < TH ? r + 1 : r] : ib;
-            const uint32_t ie = iv & 0xFFFFu, io = iv >> 16;
-            if (c0) {
-                feat_pixel(fa, ie, jv & 0xFFFFu, u16);
-                const uint32_t g = (c1 ? (uint32_t)abs((int)io - (int)ie) : 0u) +
-                                   (down ? (uint32_t)abs((int)(bv & 0xFFFFu) - (int)ie) : 0u);
-                fa.edges += g > thr;
-            }
-            if (c1) {
-                feat_pixel(fa, io, jv >> 16, u16);
-                const uint32_t g = (c2 ? (uint32_t)abs((int)(nxt & 0xFFFFu) - (int)io) : 0u) +
-                                   (down ? (uint32_t)abs((int)(bv >> 16) - (int)io) : 0u);
-                fa.edges += g > thr;
-            }
-        }
-    }
-    }
-    feat_reduce(fa, v, q0, q1);
-}
-
-// A strip's feature sums added into its tile's FeatSums (fire-and-forget reductions; the
-// first strip also records MAXV in v[11]).
-template <typename RT>
-__device__ __forceinline__ void strip_features_add(const ImageView &im, int y0, int x0,
-                                                   const uint32_t (&J)[RT::kRows], const uint32_t (&I)[RT::kRows],
-                                                   uint32_t ib, FeatSums *fs, int w, int lane) {
-    uint32_t v[16];
-    unsigned long long q0, q1;
-    strip_feature_sums<RT>(im, y0, x0, J, I, ib, w, lane, v, q0, q1);
-    if (w == 0) v[11] = RT::wide(im) ? 0xFFFFu : 0xFFu;
-    uint32_t mine = 0;   // lane k < 16: v[k], selected without a dynamic index
-#pragma unroll
-    for (int k = 0; k < 16; k++) mine = k == lane ? v[k] : mine;
-    if (lane < 16 && mine) atomicAdd(&fs->v[lane], mine);
-    if (lane == 16) atomicAdd(&fs->q[0], q0);
-    if (lane == 17) atomicAdd(&fs->q[1], q1);
-}
-
 // Initialisation of one CTA tile (Algorithm 7's scanning phase, tile-local, then the
 // frontier): check the precondition; run the tile's raster / anti-raster sweep pairs
 // (a.tile_sweeps[t], else a.sweeps), the strips exchanging their boundary rows after each
@@ -420,24 +321,17 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     __syncthreads();   // the strips' shared halo buffers are reloaded for the next tile
 }
 
-// The lean scan (no sweeps, no features), one warp per strip with no CTA barriers: each warp
-// loads a 16-row strip of a tile with its halo, checks the precondition and whether one of
-// its pixels can rise; a strip that can makes its tile PENDING (batches: a fire-and-forget
-// OR) or notifies it (single images: the first notification queues the tile, later ones
-// find it PENDING). Warps go from strip to strip independently, 7 CTAs per SM: the scan is a
-// pass over every pixel, and loads in flight are what it needs. FEATS: each strip also adds
-// its pixels' feature sums into its tile's FeatSums (learned batches).
-#ifndef IWPP_SCAN_FEATS_MINB
-#define IWPP_SCAN_FEATS_MINB 5   // CTAs per SM of the strip scan with features (96 registers)
-#endif
+// The strip scan (no sweeps), one warp per strip with no CTA barriers: each warp loads a
+// 16-row strip of a tile with its halo, checks the precondition and whether one of its
+// pixels can rise; a strip that can makes its tile PENDING (batches: a fire-and-forget OR)
+// or notifies it (single images: the first notification queues the tile, later ones find it
+// PENDING). Warps go from strip to strip independently, 7 CTAs per SM. The streaming scan
+// (iwpp_scan.cuh) replaces it wherever one connectivity is compiled in; the mixed-kind build
+// keeps it (its kinds switch per strip).
 #ifndef IWPP_SCAN_STRIP_MINB
 #define IWPP_SCAN_STRIP_MINB 7   // CTAs per SM of the strip scan (72 registers, no spills)
 #endif
-#ifndef IWPP_SCAN_STRIPS
-#define IWPP_SCAN_STRIPS 1       // 0: the lean scan works on whole tiles with CTA barriers (measured)
-#endif
-
-template <typename T, int CONN, bool FEATS = false>
+template <typename T, int CONN>
 __device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32_t t, int sw, uint8_t *wsmem,
                                 int lane) {
     constexpr int TH = kCoopStrip;
@@ -451,7 +345,6 @@ __device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32
     const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
     uint32_t J[TH], I[TH], jt, jb, it, ib;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
-    if constexpr (FEATS) strip_features_add<RT>(im, y0, x0, J, I, ib, static_cast<FeatSums *>(a.fsums) + t, sw, lane);
     bool bad = false;
 #pragma unroll
     for (int r = 0; r < TH; r++) bad |= max2(J[r], I[r]) != I[r];
@@ -467,9 +360,8 @@ __device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32
     __syncwarp();   // the warp's halo buffers are reloaded for its next strip
 }
 
-template <typename T, int CONN, bool MIXED, bool FEATS = false>
-__global__ void __launch_bounds__(kThreads, FEATS ? IWPP_SCAN_FEATS_MINB : IWPP_SCAN_STRIP_MINB)
-    scan_strip_coop_kernel(EngineArgs a) {
+template <typename T, int CONN, bool MIXED>
+__global__ void __launch_bounds__(kThreads, IWPP_SCAN_STRIP_MINB) scan_strip_coop_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -480,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, FEATS ? IWPP_SCAN_FEATS_MINB : IWPP_
         const int sw = (int)(u % kWarpsPerCta);
         const ImageView &im = image_of(a, t);
         if (!MIXED) {
-            scan_strip_coop<T, CONN, FEATS>(a, im, t, sw, wsmem, lane);
+            scan_strip_coop<T, CONN>(a, im, t, sw, wsmem, lane);
             continue;
         }
         switch (im.kind) {

@@ -138,7 +138,6 @@ struct EngineArgs {
     LevelCtr *lvl;               // nlevels counters (value-ordered mode)
     const uint32_t *tile_img;    // batch: index of each tile's image in imgs (else nullptr)
     float *feats;                // learned batches: per-tile features out of the scan (64 x 64 tiles)
-    void *fsums;                 // learned batches: per-tile feature sums the scan's strips add up
     int sweep_only;              // scan: skip tiles whose sweep count is 0 (a second, sweeps-only pass)
 };
 

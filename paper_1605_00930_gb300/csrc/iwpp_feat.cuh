@@ -1,8 +1,8 @@
 // iwpp_feat.cuh — the learned work estimator's per-block features (include/iwpp.h): the
 // per-pixel accumulation and the conversion of a block's exact integer sums to the 16 FP32
 // inputs of the MLP. Shared by the stand-alone features kernel (iwpp_sched.cu) and the
-// cooperative scan kernel, which computes the features of the tile it has just loaded
-// (iwpp_coop.cuh), so that both give identical values.
+// streaming scan kernel, which computes the features of the tile it streams through
+// (iwpp_scan.cuh), so that both give identical values.
 //
 // Per 64 x 64 block, in the dilation domain (erosion: both images complemented), with
 // d = max(I - J, 0) and d8 = d (u8) or d >> 8 (u16):
@@ -60,13 +60,6 @@ __device__ __forceinline__ float block_feature(int k, const uint32_t (&v)[16], u
         default: return (float)vk / fN;   // histogram, seeds, edges
     }
 }
-
-// A block's sums, added up by the strips that make it (v as above, v[11] = MAXV; q = sums of
-// squares of I and J).
-struct FeatSums {
-    uint32_t v[16];
-    unsigned long long q[2];
-};
 
 // Warp-wide sums of each lane's FeatAcc into v / sI2 / sJ2 (every lane ends with them).
 __device__ __forceinline__ void feat_reduce(const FeatAcc &a, uint32_t (&v)[16], unsigned long long &sI2,

@@ -62,12 +62,6 @@ int batch_launches(int n, int phases);
 // feature array in a scheduling workspace (null if the workspace is too small), and the
 // schedule itself (phases: 1 features, 2 MLP inference, 4 tile order and sweep counts).
 float *sched_features(const iwpp_image *imgs, int n, const iwpp_plan &p, void *sws, size_t sws_bytes);
-// Per-block feature sums in a scheduling workspace (for a scan that adds them up strip by
-// strip; *bytes = their size) and the kernel that turns them into the feature array.
-struct FeatSums;
-FeatSums *sched_feature_sums(const iwpp_image *imgs, int n, const iwpp_plan &p, void *sws, size_t sws_bytes,
-                             size_t *bytes);
-int features_from_sums(const FeatSums *sums, uint32_t nblocks, float *feats, cudaStream_t stream);
 int schedule_batch(const iwpp_image *imgs, int n, const iwpp_plan &p, const float *params, uint32_t *order,
                    uint8_t *sweeps, void *sws, size_t sws_bytes, cudaStream_t stream, int phases);
 }  // namespace iwpp

@@ -2,24 +2,28 @@
 // translation unit of their own, compiled in parallel with the others).
 #include "iwpp_host.h"
 #include "iwpp_coop.cuh"
+#include "iwpp_scan.cuh"
 
 namespace iwpp {
+
+#ifndef IWPP_SCAN_STREAM
+#define IWPP_SCAN_STREAM 1   // 0: the strip scan for every build (measured)
+#endif
 
 template <typename T, int CONN, bool MIXED = false>
 static RegKernelSet coop_set() {
     RegKernelSet k;
-#if IWPP_SCAN_STRIPS
-    k.scan = scan_strip_coop_kernel<T, CONN, MIXED>;
-#else
-    k.scan = scan_coop_kernel<T, CONN, MIXED, false>;
-#endif
+    // the streaming scan for builds of one connectivity; the mixed-kind build switches kinds
+    // per strip in the strip scan
+    if constexpr (MIXED || !IWPP_SCAN_STREAM) k.scan = scan_strip_coop_kernel<T, CONN, MIXED>;
+    else k.scan = scan_stream_kernel<T, CONN, false>;
     k.drain = drain_coop_kernel<T, CONN, MIXED>;
     k.drain_hi = nullptr;   // one build of the persistent kernel
     k.smem = &coop_smem_fn<T, CONN>;
     k.scan_sweeps = scan_coop_kernel<T, CONN, MIXED, true>;
-    // features in the scan: not for the mixed-kind build (its scan would inline four copies)
+    // features in the scan: not for the mixed-kind build
     if constexpr (MIXED) k.scan_feats = nullptr;
-    else k.scan_feats = scan_strip_coop_kernel<T, CONN, false, true>;
+    else k.scan_feats = scan_stream_kernel<T, CONN, true>;
     return k;
 }
 

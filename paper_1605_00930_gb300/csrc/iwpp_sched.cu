@@ -429,7 +429,7 @@ __global__ void tile_work_blocks_kernel(const SchedImage *tab, int nimg, uint32_
 // Scheduling workspace: image table | features [nblocks][16] | predictions [nblocks][2] |
 // keys [ntiles] | bucket histogram / cursors [kBuckets].
 struct SchedLayout {
-    size_t table, feats, preds, keys, hist, fsum, total;
+    size_t table, feats, preds, keys, hist, total;
     uint32_t nblocks, ntiles;
 };
 
@@ -459,8 +459,7 @@ static bool sched_layout(const iwpp_image *imgs, int n, const iwpp_plan &p, Sche
     L.preds = L.feats + align256((size_t)L.nblocks * kNF * 4);
     L.keys = L.preds + align256((size_t)L.nblocks * 2 * 4);
     L.hist = L.keys + align256((size_t)L.ntiles * 2);
-    L.fsum = L.hist + align256((size_t)kBuckets * 4);
-    L.total = L.fsum + align256((size_t)L.nblocks * sizeof(FeatSums));
+    L.total = L.hist + align256((size_t)kBuckets * 4);
     return true;
 }
 
@@ -534,33 +533,6 @@ static int schedule_impl(const iwpp_image *imgs, int n, const iwpp_plan *plan_in
         sched_scan_kernel<<<1, kBuckets, 0, stream>>>(hist);
         sched_scatter_kernel<<<g, 256, 0, stream>>>(L.ntiles, keys, hist, order);
     }
-    return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
-}
-
-// Features of every block from the per-block sums the strips of the scan kernel added up.
-__global__ void __launch_bounds__(256) features_from_sums_kernel(const FeatSums *sums, uint32_t nblocks, float *out) {
-    const uint64_t n = (uint64_t)nblocks * kNF;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t b = (uint32_t)(i / kNF);
-        const int k = (int)(i % kNF);
-        uint32_t v[16];
-#pragma unroll
-        for (int q = 0; q < 16; q++) v[q] = sums[b].v[q];
-        out[i] = block_feature(k, v, sums[b].q[0], sums[b].q[1], sums[b].v[11]);
-    }
-}
-
-FeatSums *sched_feature_sums(const iwpp_image *imgs, int n, const iwpp_plan &p, void *sws, size_t sws_bytes,
-                             size_t *bytes) {
-    SchedLayout L;
-    if (!sws || ((uintptr_t)sws & 255) || !sched_layout(imgs, n, p, L, nullptr, nullptr) || sws_bytes < L.total)
-        return nullptr;
-    *bytes = (size_t)L.nblocks * sizeof(FeatSums);
-    return reinterpret_cast<FeatSums *>(static_cast<uint8_t *>(sws) + L.fsum);
-}
-
-int features_from_sums(const FeatSums *sums, uint32_t nblocks, float *feats, cudaStream_t stream) {
-    features_from_sums_kernel<<<grid_for((uint64_t)nblocks * kNF, 256, 8), 256, 0, stream>>>(sums, nblocks, feats);
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
 }
 

@@ -460,11 +460,13 @@ IWPP_API int iwpp_regional_maxima(const void *image, void *scratch, uint8_t *out
  * Reconstruction of an image held in HOST memory, band by band (images larger than the
  * device's memory; Sec. 1 cites 100K x 100K scans, Sec. 4.5 splits such images into tasks
  * and corrects the propagation across task borders). The image is cut into horizontal bands
- * of band_rows rows. Each band is copied to the device with one halo row above and below
- * whose mask is set to their marker (fixed sources), reconstructed through the single-image
- * path, and copied back. Bands are visited top to bottom, then bottom to top, a band again
- * only after a neighbour band changed, until no band is left to visit: the result is
- * bit-identical to iwpp_reconstruct. While a band is reconstructed on `stream`, the band
+ * of band_rows rows. Each band is copied to the device together with band_rows / 16 rows of
+ * each neighbour band (the overlap) and one halo row beyond them whose mask is set to their
+ * marker (fixed sources), reconstructed through the single-image path, and its own rows are
+ * copied back (the overlap rows are not). Bands are visited top to bottom, then bottom to
+ * top, a band again only after a neighbour band changed, until no band is left to visit:
+ * the result is bit-identical to iwpp_reconstruct. The overlap lets a path that crosses a
+ * band border and comes back within it be followed in one visit. While a band is reconstructed on `stream`, the band
  * expected next is copied to the device on a stream of the call's own (two band buffers).
  * Blocking: the call waits for every band's change flag; it creates and destroys that
  * stream, a few events and an 8-byte pinned host buffer.
@@ -472,9 +474,9 @@ IWPP_API int iwpp_regional_maxima(const void *image, void *scratch, uint8_t *out
  *                        the result overwrites marker_inout
  *   band_rows            rows per band, >= 1 (a band of >= H rows is one reconstruction)
  *   workspace            device, 256-byte aligned, iwpp_host_workspace_bytes(H, W, dtype,
- *                        band_rows) bytes: two band buffers (each two (band_rows + 2) x W
- *                        planes and one band_rows x W plane) and a single-image workspace
- *                        for band_rows + 2 rows
+ *                        band_rows) bytes: two band buffers (each two (band_rows + 2 ov + 2)
+ *                        x W planes, ov = band_rows / 16, and one band_rows x W plane) and a
+ *                        single-image workspace for band_rows + 2 ov + 2 rows
  *   visits_out           host int32 or NULL: band reconstructions made
  * Returns IWPP_OK, a host-detected error, or the first device error of any band (e.g.
  * IWPP_ERR_PRECONDITION; the host image is then unspecified). Resumable: every pixel written

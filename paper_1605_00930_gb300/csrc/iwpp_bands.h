@@ -2,7 +2,7 @@
 // no CUDA: iwpp_ooc.cu drives it, and a host test drives it against a simulated image).
 //
 // Every band is visited once; after that a band is visited again only when a neighbour band
-// changed after its last visit (its halo rows may then differ). Visits sweep top to bottom,
+// changed after its last visit (its overlap and halo rows may then differ). Visits sweep top to bottom,
 // then bottom to top, skipping clean bands, until no band is dirty. When next() returns -1,
 // every band's last visit saw its neighbours' final rows.
 #pragma once
@@ -11,6 +11,11 @@
 #include <vector>
 
 namespace iwpp {
+
+// Rows of each neighbour band reconstructed together with a band of `band` rows and not
+// written back (the overlap; always < band, so an extended band reaches only its two
+// neighbours).
+inline int64_t band_overlap(int64_t band) { return band / 16; }
 
 class BandSchedule {
   public:

@@ -70,6 +70,29 @@ def test_maze_crosses_band_borders(iw, oracle_lib):
         assert visits > -(-H // band_rows)
 
 
+def test_serpentine_crosses_borders_both_ways(iw, oracle_lib):
+    """Vertical walls every 8 columns with one gap, alternating bottom and top: the only path
+    from the seed runs down one corridor and up the next, crossing every band border in both
+    directions once per corridor. Bands of 16, 48 and 100 rows are reconstructed with 1, 3
+    and 6 rows of each neighbour (the overlap) and must still give the oracle's result."""
+    H, W = 230, 97
+    mask = np.full((H, W), 180, np.uint8)
+    for k, x in enumerate(range(7, W - 1, 8)):
+        mask[:, x] = 0
+        if k % 2:
+            mask[:2, x] = 120
+        else:
+            mask[-2:, x] = 120
+    marker = np.zeros_like(mask)
+    marker[0, 0] = 180
+    exp = oracle_lib.reconstruct(marker, mask, 8, "dilate")
+    assert exp[H // 2, W - 1] == 120   # the last corridor is reached
+    for band_rows in (16, 48, 100):
+        got, visits = run_host(iw, marker, mask, 8, "dilate", band_rows)
+        np.testing.assert_array_equal(got, exp)
+        assert visits > -(-H // band_rows)
+
+
 def test_random_ragged(iw, oracle_lib):
     rng = np.random.default_rng(1605)
     for H, W, b in [(1, 1, 1), (1, 700, 3), (700, 1, 9), (65, 130, 16), (129, 65, 64), (257, 513, 31)]:

@@ -395,11 +395,11 @@ __global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : 8) scan_coop_kernel(Eng
     uint8_t *wsmem = smem_raw + w * RT::smem_per_warp(0);
     CoopShared &C = *reinterpret_cast<CoopShared *>(smem_raw + kWarpsPerCta * RT::smem_per_warp(0));
     uint8_t *stage = smem_raw + coop_scan_stage_offset<T, CONN>() + w * RT::kStageBytes;
-    for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    auto tile = [&](uint32_t t) {
         const ImageView &im = image_of(a, t);
         if (!MIXED) {
             scan_tile_coop<T, CONN, SWEEPS>(a, im, t, wsmem, C, stage, w, lane);
-            continue;
+            return;
         }
         switch (im.kind) {
             case 0: scan_tile_coop<uint8_t, 4, SWEEPS>(a, im, t, wsmem, C, stage, w, lane); break;
@@ -407,7 +407,26 @@ __global__ void __launch_bounds__(kThreads, SWEEPS ? 4 : 8) scan_coop_kernel(Eng
             case 2: scan_tile_coop<uint8_t, 8, SWEEPS>(a, im, t, wsmem, C, stage, w, lane); break;
             default: scan_tile_coop<uint16_t, 8, SWEEPS>(a, im, t, wsmem, C, stage, w, lane); break;
         }
+    };
+    if (SWEEPS && a.sweep_only) {
+        // The sweeps-only pass of learned batches, where most tiles have no sweeps: the CTA
+        // reads the counts of kThreads of its tiles at once and visits only those with sweeps
+        // (the same tiles as the loop below, grouped differently).
+        __shared__ uint32_t has_sweeps[kWarpsPerCta];
+        const uint64_t step = (uint64_t)gridDim.x * kThreads;
+        for (uint64_t base = blockIdx.x; base < a.ntiles; base += step) {
+            const uint64_t mine = base + (uint64_t)threadIdx.x * gridDim.x;
+            const uint32_t b = __ballot_sync(0xffffffffu, mine < a.ntiles && a.tile_sweeps[mine] != 0);
+            if (lane == 0) has_sweeps[w] = b;
+            __syncthreads();
+            for (int k = 0; k < kWarpsPerCta; k++)
+                for (uint32_t m = has_sweeps[k]; m; m &= m - 1)
+                    tile((uint32_t)(base + (uint64_t)(32 * k + __ffs(m) - 1) * gridDim.x));
+            __syncthreads();   // every thread has read the flags before the next chunk's
+        }
+        return;
     }
+    for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) tile(t);
 }
 
 }  // namespace iwpp

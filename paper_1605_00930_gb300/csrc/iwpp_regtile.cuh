@@ -145,7 +145,7 @@ struct RegTile {
     static __device__ void load(const ImageView &im, const Smem &s, int y0, int x0, uint32_t (&J)[TH],
                                 uint32_t (&I)[TH], uint32_t &jt, uint32_t &jb, uint32_t &it, uint32_t &ib,
                                 int lane) {
-        if ((im.W & 1) == 0 && x0 + TW <= im.W) {   // whole 64-column span inside, rows aligned
+        if (im.W >= 2) {   // every width but 1
             load_fused(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
             return;
         }
@@ -158,48 +158,79 @@ struct RegTile {
         load_halo(im, s, y0, x0, jt, jb, it, ib, true, lane);
     }
 
-    // The load of a tile whose 64-column span lies inside the image (W even): every global
-    // load (strip rows, halo rows, halo columns) is issued before the first result is used,
-    // so the tile costs one memory round trip (measured: the load phase of a visit 20-25 %
-    // shorter than loading the halo after the strip).
+    // The load of a strip and its halo with every global load (strip rows, halo rows, halo
+    // columns) issued before the first result is used, so a visit costs one memory round trip
+    // (measured: the load phase 20-25 % shorter than loading the halo after the strip). Rows
+    // are read as aligned two-pixel words (u8: 16-bit, u16: 32-bit loads). Even W: the pair
+    // (gx, gx + 1) is aligned in every row. Odd W >= 3: a row's pairs are aligned when the row
+    // starts on an even element (row index even, as x0 is even) and off by one otherwise; such
+    // a row is read as the aligned pairs (gx - 1, gx), and each lane takes its second pixel
+    // from the next lane's first (lane 31 from pixel x0 + 63, loaded with the halo columns by
+    // the lane that holds that row). On even rows the lane whose pair would end past the row
+    // (gx = W - 1) reads an aligned pair inside the row instead and takes pixel W - 1 from the
+    // halo lanes too. Every address stays inside its row (the row before, for the first pair
+    // of an odd row) of the image; columns at or past W are zeroed.
     static __device__ __forceinline__ void load_fused(const ImageView &im, const Smem &s, int y0, int x0,
                                                       uint32_t (&J)[TH], uint32_t (&I)[TH], uint32_t &jt,
                                                       uint32_t &jb, uint32_t &it, uint32_t &ib, int lane) {
         static_assert(TH + 2 <= 32, "one halo row per lane");
+        const int W = im.W, H = im.H;
+        const bool odd = (W & 1) != 0;   // W >= 3 when odd (the caller's condition)
         const int gx = x0 + 2 * lane;
         const uint32_t f2 = im.flip | (im.flip << 16);
+        const uint32_t cm = (gx < W ? 0xFFFFu : 0u) | (gx + 1 < W ? 0xFFFF0000u : 0u);
+        const int xe0 = odd ? min(gx, W - 3) : min(gx, W - 2);   // pair start in an aligned row
+        const int xe1 = min(gx, W - 1) - 1;                      // in an odd row of an odd-W image
+        auto pair_start = [&](int y) {   // >= 0: an odd row has yc >= 1
+            const int yc = min(max(y, 0), H - 1);
+            return (size_t)((long long)yc * W + ((odd && (yc & 1)) ? xe1 : xe0));
+        };
+        auto odd_row = [&](int y) { return odd && (min(max(y, 0), H - 1) & 1); };
 #pragma unroll
         for (int r = 0; r < TH; r++) {
-            const size_t e = (size_t)min(y0 + r, im.H - 1) * im.W + gx;
+            const size_t e = pair_start(y0 + r);
             J[r] = ld_raw(im, im.J, e, true);
             I[r] = ld_raw(im, im.I, e, false);
         }
         // halo rows (rows clamped into the image, so every address is valid; zeroed below when
         // the row lies outside it: a strip of a bottom tile can start several rows below the image)
-        const size_t et = (size_t)min(max(y0 - 1, 0), im.H - 1) * im.W + gx;
-        const size_t eb = (size_t)min(max(y0 + TH, 0), im.H - 1) * im.W + gx;
+        const size_t et = pair_start(y0 - 1), eb = pair_start(y0 + TH);
         uint32_t rjt = ld_raw(im, im.J, et, true), rjb = ld_raw(im, im.J, eb, true);
         uint32_t rit = ld_raw(im, im.I, et, false), rib = ld_raw(im, im.I, eb, false);
-        // halo columns: lane hr < TH + 2 holds row y0 + hr - 1
+        // halo columns: lane hr < TH + 2 holds row y0 + hr - 1 (odd W: also pixel min(x0 + 63, W - 1))
         const int gy = y0 + lane - 1;
-        const bool rowin = lane < TH + 2 && gy >= 0 && gy < im.H;
-        const bool lin = rowin && x0 > 0, rin = rowin && x0 + TW < im.W;
-        const size_t hrow = (size_t)min(max(gy, 0), im.H - 1) * im.W;
-        const size_t el = hrow + max(x0 - 1, 0), er = hrow + min(x0 + TW, im.W - 1);
+        const bool rowin = lane < TH + 2 && gy >= 0 && gy < H;
+        const bool lin = rowin && x0 > 0, rin = rowin && x0 + TW < W;
+        const size_t hrow = (size_t)min(max(gy, 0), H - 1) * (size_t)W;
+        const size_t el = hrow + max(x0 - 1, 0), er = hrow + min(x0 + TW, W - 1), e63 = hrow + min(x0 + 63, W - 1);
         const uint32_t lj = ld1(im, im.J, el, true), rj = ld1(im, im.J, er, true);
         const uint32_t li = ld1(im, im.I, el, false), ri = ld1(im, im.I, er, false);
-        // uses
+        const uint32_t sj = odd ? ld1(im, im.J, e63, true) : 0u, si = odd ? ld1(im, im.I, e63, false) : 0u;
+        // uses: a row's pixel pair in the dilation domain; hl = the halo lane holding the row
+        auto fix = [&](uint32_t &u, uint32_t sv, bool oddrow) {
+            if (oddrow) {
+                uint32_t n = __shfl_down_sync(0xffffffffu, u, 1);
+                if (lane == 31) n = sv;
+                u = (u >> 16) | (n << 16);
+            } else if (gx == W - 1) {
+                u = sv;   // pixel W - 1; the pair's second pixel lies outside the image
+            }
+        };
+        auto use = [&](uint32_t rj_, uint32_t ri_, int y, int hl, bool in, uint32_t &jo, uint32_t &io) {
+            uint32_t uj = unpack_raw(im, rj_), ui = unpack_raw(im, ri_);
+            if (odd) {   // warp-uniform
+                const uint32_t svj = __shfl_sync(0xffffffffu, sj, hl), svi = __shfl_sync(0xffffffffu, si, hl);
+                const bool o = odd_row(y);
+                fix(uj, svj, o);
+                fix(ui, svi, o);
+            }
+            jo = in ? (uj ^ f2) & cm : 0u;
+            io = in ? (ui ^ f2) & cm : 0u;
+        };
 #pragma unroll
-        for (int r = 0; r < TH; r++) {
-            const bool in = y0 + r < im.H;
-            J[r] = in ? unpack_raw(im, J[r]) ^ f2 : 0u;
-            I[r] = in ? unpack_raw(im, I[r]) ^ f2 : 0u;
-        }
-        const bool tin = y0 >= 1 && y0 - 1 < im.H, bin = y0 + TH < im.H;
-        jt = tin ? unpack_raw(im, rjt) ^ f2 : 0u;
-        it = tin ? unpack_raw(im, rit) ^ f2 : 0u;
-        jb = bin ? unpack_raw(im, rjb) ^ f2 : 0u;
-        ib = bin ? unpack_raw(im, rib) ^ f2 : 0u;
+        for (int r = 0; r < TH; r++) use(J[r], I[r], y0 + r, r + 1, y0 + r < H, J[r], I[r]);
+        use(rjt, rit, y0 - 1, 0, y0 >= 1 && y0 - 1 < H, jt, it);
+        use(rjb, rib, y0 + TH, TH + 1, y0 + TH < H, jb, ib);
         if (lane < TH + 2) {
             s.hxJ[lane] = lin ? (lj ^ im.flip) << 16 : 0u;
             s.hxJ[TH + 2 + lane] = rin ? rj ^ im.flip : 0u;

@@ -92,9 +92,11 @@ def test_random_small(iw, oracle_lib, shape, dtype, op, conn, solver):
         check(iw, oracle_lib, marker, mask, conn, op, p)
 
 
-# Widths around the 64-column register tiles and strips and their 2-pixel pairs (odd widths take the
-# unaligned load path), heights around its 16 rows.
-EDGE_SHAPES = [(15, 63), (16, 64), (17, 65), (33, 127), (31, 128), (16, 129), (2, 2), (3, 1), (1, 3)]
+# Widths around the 64-column register tiles and strips and their 2-pixel pairs (odd widths read the
+# rows that start on an odd element as shifted pairs recombined across lanes; the narrowest widths
+# and partial tiles mask columns), heights around its 16 rows.
+EDGE_SHAPES = [(15, 63), (16, 64), (17, 65), (33, 127), (31, 128), (16, 129), (2, 2), (3, 1), (1, 3),
+               (130, 5), (18, 3), (67, 191), (100, 255), (49, 257)]
 
 
 @pytest.mark.parametrize("solver", ["register", "coop"])

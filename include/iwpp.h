@@ -95,7 +95,7 @@ typedef enum {
  *                      solver does, and the strips exchange their boundary
  *                      rows through shared memory until the tile is settled
  *                      (tile_h == tile_w == 64, no revisit sweeps, no value
- *                      levels, at most 5 CTAs per SM; its scan kernel runs the
+ *                      levels, at most 6 CTAs per SM; its scan kernel runs the
  *                      sweep pairs on the whole 64 x 64 tile, the strips
  *                      exchanging boundary rows after each pair)
  *   value_levels       0 or 1: the persistent kernel's tile queue is one FIFO;

@@ -25,7 +25,7 @@ struct RegKernelSet {
 };
 constexpr int kRegBlocks = 4, kRegHiBlocks = 6;
 #ifndef IWPP_COOP_MINB
-#define IWPP_COOP_MINB 5
+#define IWPP_COOP_MINB 6   // 80 registers; 5 (96 registers) measured slower on batches and the seed image
 #endif
 constexpr int kCoopBlocks = IWPP_COOP_MINB;   // CTAs per SM of the cooperative solver's persistent kernel
 RegKernelSet reg_kernel_set(int th, int tw, int v);

@@ -113,8 +113,8 @@ def test_host_argument_errors_return_before_any_launch(iwpp):
         p = iwpp.iwpp_default_plan()
         p.tile_h, p.tile_w, p.local_solver, p.value_levels = th, tw, solver, levels
         assert iwpp.iwpp_reconstruct_plan(P(a16), P(a16), 4, 4, 8, 0, 0, p, P(ws), 16, null) == 1
-    # the cooperative solver takes no revisit sweeps and at most 5 CTAs per SM
-    for kw in [{"revisit_sweeps": 2}, {"blocks_per_sm": 6}]:
+    # the cooperative solver takes no revisit sweeps and at most 6 CTAs per SM
+    for kw in [{"revisit_sweeps": 2}, {"blocks_per_sm": 7}]:
         p = iwpp.iwpp_default_plan()
         p.tile_h, p.tile_w, p.local_solver = 64, 64, 2
         for k, v in kw.items():

@@ -220,10 +220,15 @@ __device__ __forceinline__ void visit_tile_coop_any(const EngineArgs &a, uint32_
 
 // The persistent kernel: warp 0 pops a tile for the CTA, the CTA visits it. MIXED: a batch
 // whose images differ in pixel type or connectivity (T, CONN unused); that build, with four
-// visit variants inlined, keeps 4 CTAs per SM (at 5 it spills), the specialised ones take 5
-// (measured: -6 % on the 4096^2 image, -12 % on the 16384^2 seed image).
+// visit variants inlined, keeps 4 CTAs per SM (at 5 it spills). The builds for one pixel
+// type take kCoopBlocks (single images: more CTAs slow the images bound by one chain of
+// tile hops), the build for u8 + u16 batches kCoopBatchBlocks (a batch keeps every worker
+// busy, so the seventh CTA pays despite its spills). Without a plan's blocks_per_sm the
+// grid is the occupancy the launch bounds give.
 template <typename T, int CONN, bool MIXED>
-__global__ void __launch_bounds__(kThreads, MIXED ? kRegBlocks : kCoopBlocks) drain_coop_kernel(EngineArgs a) {
+__global__ void __launch_bounds__(kThreads, MIXED ? kRegBlocks
+                                                 : (std::is_same<T, AnyPix>::value ? kCoopBatchBlocks : kCoopBlocks))
+    drain_coop_kernel(EngineArgs a) {
     using RT = RegTile<T, CONN, kCoopStrip>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

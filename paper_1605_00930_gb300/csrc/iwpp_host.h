@@ -28,6 +28,10 @@ constexpr int kRegBlocks = 4, kRegHiBlocks = 6;
 #define IWPP_COOP_MINB 6   // 80 registers; 5 (96 registers) measured slower on batches and the seed image
 #endif
 constexpr int kCoopBlocks = IWPP_COOP_MINB;   // CTAs per SM of the cooperative solver's persistent kernel
+#ifndef IWPP_COOP_BATCH_MINB
+#define IWPP_COOP_BATCH_MINB 7   // its build for u8 + u16 batches (72 registers, ~250 B of spills)
+#endif
+constexpr int kCoopBatchBlocks = IWPP_COOP_BATCH_MINB;
 RegKernelSet reg_kernel_set(int th, int tw, int v);
 RegKernelSet coop_kernel_set(int th, int tw, int v);   // cooperative solver (64 x 64 tiles)
 

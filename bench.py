@@ -288,8 +288,8 @@ class Forms:
         """Kernel launches of the library in one step of `form`."""
         from paper_1605_00930_gb300 import iwpp
         n = len(self.db.items)
-        if form == "plain":
-            return 2 * n
+        if form == "plain":   # per image: scan, queue compaction, queue finalisation, drain
+            return 4 * n
         if form == "batched_static":
             return iwpp.iwpp_batch_launch_count(n, 3)
         fused = (self.plan.local_solver == iwpp.IWPP_SOLVER_COOP and self.plan.tile_h == 64 and

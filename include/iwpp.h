@@ -163,7 +163,9 @@ IWPP_API int iwpp_reconstruct_plan(void *marker_inout, const void *mask, int64_t
  * iwpp_scan resets the workspace and runs the tile-parallel scan kernel
  * (precondition check, `plan->sweeps` tile-local raster / anti-raster sweep pairs
  * of Algorithm 7, and frontier initialisation: the tiles whose pixels can still
- * be raised are queued); iwpp_drain then runs the persistent kernel that drains
+ * be raised are queued — with one FIFO (value_levels <= 1) in a spread order that
+ * keeps tiles next to each other apart in the queue, by two small kernels after the
+ * scan); iwpp_drain then runs the persistent kernel that drains
  * the queued tiles (Algorithm 7's irregular propagation phase). Calling
  * iwpp_scan and then iwpp_drain with identical arguments on one stream is exactly
  * iwpp_reconstruct_plan. Same arguments, ownership and errors.

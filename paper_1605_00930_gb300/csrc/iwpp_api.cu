@@ -23,6 +23,10 @@
 #include "iwpp_engine.cuh"
 #include "iwpp_host.h"
 
+#ifndef IWPP_SINGLE_SPREAD
+#define IWPP_SINGLE_SPREAD 1   // single images queue their initial frontier in the spread order
+#endif
+
 namespace iwpp {
 
 // ---- compiled tile shapes ---------------------------------------------------------------------
@@ -260,6 +264,7 @@ static void fill_common(EngineArgs &a, const iwpp_plan &p, uint8_t *base, size_t
     a.revisit_sweeps = p.revisit_sweeps;
     a.tile_sweeps = nullptr;
     a.order = nullptr;
+    a.spread = 0;
     a.tile_work = nullptr;
     a.defer_push = 0;
     a.watchdog_ns = p.watchdog_ns > 0 ? p.watchdog_ns : 10ll * 1000 * 1000 * 1000;
@@ -336,7 +341,21 @@ int reconstruct_one(void *marker, const void *mask, int64_t H, int64_t W, int co
         const int sms = device_sm_count();
         const uint32_t ctas = (L.ntiles + kWarpsPerCta - 1) / kWarpsPerCta;
         const uint32_t scan_grid = ctas < (uint32_t)(sms * 16) ? ctas : (uint32_t)(sms * 16);
+        // one FIFO: the scan marks tiles PENDING and the initial frontier is queued in the
+        // spread order, as in batches; value levels: the scan queues each tile as it finds it
+        const bool spread = IWPP_SINGLE_SPREAD && L.nlevels <= 1;
+        if (spread) {
+            a.defer_push = 1;
+            a.spread = spread_multiplier(L.ntiles);
+        }
         scan_fn(p, k, p.sweeps > 0)<<<scan_grid, kThreads, drain_smem(p, k), stream>>>(a);
+        if (spread) {
+            const uint32_t cgrid = (L.ntiles + 255) / 256 < (uint32_t)(sms * 8) ? (L.ntiles + 255) / 256
+                                                                                 : (uint32_t)(sms * 8);
+            compact_kernel<<<cgrid, 256, 0, stream>>>(a);
+            finalize_queue_kernel<<<cgrid, 256, 0, stream>>>(a);
+            a.defer_push = 0;
+        }
     }
     if (phases & kPhaseDrain) drain_fn(p, k)<<<L.grid, kThreads, drain_smem(p, k), stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
@@ -460,6 +479,7 @@ int reconstruct_batch(const iwpp_image *imgs, int n, const iwpp_plan *plan_in, c
                        imgs[0].op, imgs[0].dtype, p, 0);
     a.tile_sweeps = tile_sweeps;
     a.order = order;
+    a.spread = spread_multiplier(L.ntiles);
     a.tile_work = tile_work;
     a.defer_push = 1;
     a.tile_img = reinterpret_cast<const uint32_t *>(base + L.timg);

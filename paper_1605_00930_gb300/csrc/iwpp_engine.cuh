@@ -43,6 +43,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "iwpp_spread.h"
+
 // Tuning switches (compile-time; the defaults are the measured best).
 #ifndef IWPP_DRAIN_MINB
 #define IWPP_DRAIN_MINB 4     // persistent-kernel CTAs per SM the register budget targets
@@ -131,6 +133,7 @@ struct EngineArgs {
     int revisit_sweeps;          // sweep pairs at a tile's first persistent visit
     const uint8_t *tile_sweeps;  // optional per-tile sweep pairs for the scan kernel
     const uint32_t *order;       // optional order in which the initial frontier is queued
+    uint32_t spread;             // without an order: position i queues tile (i * spread) mod ntiles (0: i)
     uint32_t *tile_work;         // optional per-tile counters: [t] pops, [ntiles + t] SM cycles
     int defer_push;              // scan kernel marks tiles PENDING; the compact kernel queues them
     long long watchdog_ns;
@@ -140,6 +143,7 @@ struct EngineArgs {
     float *feats;                // learned batches: per-tile features out of the scan (64 x 64 tiles)
     int sweep_only;              // scan: skip tiles whose sweep count is 0 (a second, sweeps-only pass)
 };
+
 
 // ---- small device helpers ------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -1185,6 +1189,13 @@ __device__ __forceinline__ void queue_warp(const EngineArgs &a, bool want, uint3
     if (want) a.queue[(base + __popc(bal & ((1u << lane) - 1u))) % a.ntiles] = t;
 }
 
+// The initial frontier of a batch is queued in `order`, else in a spread order: position i
+// takes tile (i * spread) mod ntiles, spread odd, coprime with ntiles and near 0.618 ntiles,
+// so that tiles next to each other in an image (which raster order would hand to concurrent
+// workers) are far apart in the queue. Concurrent neighbours raise each other's borders
+// while both are being visited and so revisit each other; on the 512-image batch the spread
+// order needs 21 % fewer visits than raster order (measured: as few as a random permutation
+// or an order by measured work, largest or smallest first).
 static __global__ void __launch_bounds__(256) compact_kernel(EngineArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -1193,7 +1204,7 @@ static __global__ void __launch_bounds__(256) compact_kernel(EngineArgs a) {
         uint32_t t = 0;
         bool want = false;
         if (i < a.ntiles) {
-            t = a.order ? a.order[i] : i;
+            t = a.order ? a.order[i] : spread_tile(i, a.ntiles, a.spread);
             if (t < a.ntiles && (a.state[t] & ST_PENDING) != 0)
                 want = (atomicOr(a.state + t, ST_QUEUED) & ST_QUEUED) == 0;
         }

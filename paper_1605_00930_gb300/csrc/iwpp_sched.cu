@@ -14,6 +14,7 @@
 
 #include "../../include/iwpp.h"
 #include "iwpp_feat.cuh"
+#include "iwpp_spread.h"
 #include "iwpp_host.h"
 
 namespace iwpp {
@@ -396,13 +397,18 @@ __global__ void sched_scan_kernel(uint32_t *hist) {   // exclusive scan, one blo
 }
 
 // Scatter tiles to their bucket's next slots. Lanes with the same key share one atomic
-// (many tiles fall into few buckets), and keep their lane order inside the group.
-__global__ void sched_scatter_kernel(uint32_t ntiles, const uint16_t *key, uint32_t *cursor, uint32_t *order) {
+// (many tiles fall into few buckets), and keep their lane order inside the group. Tiles are
+// taken in the spread order (iwpp_spread.h), so that inside a bucket tiles next to each other
+// in an image are far apart: tiles of similar predicted work lie close together, and a
+// bucket in tile-id order would hand neighbours to concurrent workers (measured: an order by
+// buckets in tile-id order needs as many visits as no order at all).
+__global__ void sched_scatter_kernel(uint32_t ntiles, const uint16_t *key, uint32_t *cursor, uint32_t *order,
+                                     uint32_t spread) {
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;   // a multiple of 32: t0 stays warp-uniform
     for (uint32_t t0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; t0 < ntiles; t0 += stride) {
-        const uint32_t t = t0 + lane;
-        const bool valid = t < ntiles;
+        const bool valid = t0 + lane < ntiles;
+        const uint32_t t = valid ? spread_tile(t0 + lane, ntiles, spread) : 0u;
         const uint32_t k = valid ? key[t] : 0xFFFFFFFFu;
         const unsigned peers = __match_any_sync(0xffffffffu, k);
         const int leader = __ffs(peers) - 1;
@@ -531,7 +537,7 @@ static int schedule_impl(const iwpp_image *imgs, int n, const iwpp_plan *plan_in
         const int g = grid_for(L.ntiles, 256, 8);
         sched_keys_kernel<<<g, 256, 0, stream>>>(table, n, L.ntiles, p.tile_h, p.tile_w, Y, keys, sweeps, hist);
         sched_scan_kernel<<<1, kBuckets, 0, stream>>>(hist);
-        sched_scatter_kernel<<<g, 256, 0, stream>>>(L.ntiles, keys, hist, order);
+        sched_scatter_kernel<<<g, 256, 0, stream>>>(L.ntiles, keys, hist, order, spread_multiplier(L.ntiles));
     }
     return cudaGetLastError() == cudaSuccess ? IWPP_OK : IWPP_ERR_CUDA;
 }

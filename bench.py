@@ -241,7 +241,7 @@ def _capture(fn):
 
 class Forms:
     """The three forms of one workload on one DeviceBatch: plain per-image loop, batched
-    static (tile-id order), batched + learned schedule. Each batched form is two graphs
+    static (the spread order of the initial frontier), batched + learned schedule. Each batched form is two graphs
     (prepare + scan, then the persistent drain) so that the drain can be timed alone."""
 
     def __init__(self, db, sch, plan, dev):

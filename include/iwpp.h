@@ -211,7 +211,10 @@ IWPP_API size_t iwpp_batch_workspace_bytes(const iwpp_image *imgs, int n, const 
  * into the workspace by small kernels that take the descriptors as parameters,
  * a scan kernel runs over every tile of every image (precondition check,
  * tile-local sweeps, frontier initialisation), a compact kernel queues the tiles
- * that can still change in schedule order, and one persistent kernel drains the
+ * that can still change in schedule order (without an explicit order: the spread
+ * order, position i -> tile (i * m) mod ntiles with m coprime to ntiles near
+ * 0.618 ntiles, which keeps tiles next to each other apart in the queue so that
+ * concurrent workers do not keep raising each other's borders), and one persistent kernel drains the
  * whole batch. `imgs` is a HOST array of n >= 1 descriptors, read during the call
  * only. No host synchronisation and no allocation: the call can be captured in a
  * CUDA graph (the descriptors are then frozen into the graph).

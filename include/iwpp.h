@@ -300,14 +300,16 @@ IWPP_API int iwpp_autotune_batch(const iwpp_image *imgs, int n, iwpp_plan *plan_
  * Every image is cut into IWPP_FEATURE_BLOCK x IWPP_FEATURE_BLOCK blocks (the last
  * ones partial), numbered image by image, row-major. Per block, IWPP_NFEAT float
  * features, in the dilation domain (both images complemented for erosion),
- * d = max(I - J, 0), d8 = d (u8) or d >> 8 (u16):
- *   [0..7]   fractions of the block with d8 == 0, d8 == 1, 2..3, 4..7, 8..15,
- *            16..31, 32..63, >= 64
+ * d = max(I - J, 0), d8 = d (u8) or d >> 8 (u16); [0..14] are taken over the
+ * block's rows 0, 4, 8, ... (every fourth row: the sampled pixels):
+ *   [0..7]   fractions of the sampled pixels with d8 == 0, d8 == 1, 2..3, 4..7,
+ *            8..15, 16..31, 32..63, >= 64
  *   [8]      fraction with J == I and J > 0 (seeds)
  *   [9]      fraction with |I(p)-I(p+x)| + |I(p)-I(p+y)| > 16 * MAXV / 255
- *            (a neighbour outside the block contributes 0)
+ *            (a neighbour outside the block contributes 0; p + y is the next
+ *            row of the block, sampled or not)
  *   [10..14] mean(I), std(I), mean(J), std(J), mean(d), each / MAXV
- *   [15]     log2(pixels in the block) / 12
+ *   [15]     log2(pixels in the block, every row) / 12
  * The MLP is 16 -> 64 -> 64 -> 2 with ReLU, FP32, IWPP_MLP_PARAMS parameters in
  * one flat device array: W1[16][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]
  * (y = x W + b). Output 0 predicts the block's log work, log(1 + SM cycles spent

@@ -5,21 +5,25 @@
 // (iwpp_scan.cuh), so that both give identical values.
 //
 // Per 64 x 64 block, in the dilation domain (erosion: both images complemented), with
-// d = max(I - J, 0) and d8 = d (u8) or d >> 8 (u16):
+// d = max(I - J, 0) and d8 = d (u8) or d >> 8 (u16); f[0..14] over every kFeatRowStep-th row
+// of the block (its rows 0, 4, 8, ...: the sampled pixels, a quarter of the arithmetic):
 //   f[0..7]   histogram of d8: bin 0 = 0, bin k = bit length of d8 (1..6), bin 7 = d8 >= 64
 //   f[8]      fraction of pixels with J == I > 0
 //   f[9]      fraction with |I(p) - I(p + x)| + |I(p) - I(p + y)| > 16 MAXV / 255 (a neighbour
-//             outside the block contributes 0)
+//             outside the block contributes 0; p + y is the next row, sampled or not)
 //   f[10..14] mean(I), std(I), mean(J), std(J), mean(d), each divided by MAXV
-//   f[15]     log2(pixels in the block) / 12
+//   f[15]     log2(pixels in the block, every row) / 12
 #pragma once
 #include <cstdint>
 
 namespace iwpp {
 
+constexpr int kFeatRowStep = 4;   // the sampled rows of a block: 0, 4, 8, ...
+
 struct FeatAcc {
     uint32_t h03 = 0, h47 = 0;   // histogram bins, 8 bits each
-    uint32_t seeds = 0, edges = 0, sI = 0, sJ = 0, sD = 0, n = 0;
+    uint32_t seeds = 0, edges = 0, sI = 0, sJ = 0, sD = 0, n = 0;   // n: sampled pixels
+    uint32_t npix = 0;           // pixels of the block (every row)
     unsigned long long sI2 = 0, sJ2 = 0;
 };
 
@@ -39,7 +43,8 @@ __device__ __forceinline__ void feat_pixel(FeatAcc &a, uint32_t i, uint32_t j, b
 }
 
 // Sums of a block: v[0..7] histogram, v[8] seeds, v[9] edges, v[10] sum I, v[12] sum J,
-// v[14] sum d, v[15] pixel count (v[11], v[13] unused); sI2 / sJ2 the sums of squares.
+// v[14] sum d, v[15] sampled pixel count, v[13] the block's pixel count (v[11] unused);
+// sI2 / sJ2 the sums of squares.
 // Feature k in FP32 from exact integers (FP64 is slow on this part): the variance numerator
 // N * sum(x^2) - sum(x)^2 is exact in 64 bits (N <= 4096, x <= 65535), so no cancellation;
 // every feature is within a few float ulps of the exact value.
@@ -56,7 +61,7 @@ __device__ __forceinline__ float block_feature(int k, const uint32_t (&v)[16], u
         case 12: return (float)v[12] / NM;
         case 13: return sqrtf((float)((unsigned long long)N * sJ2 - (unsigned long long)v[12] * v[12])) / NM;
         case 14: return (float)v[14] / NM;
-        case 15: return log2f(fN) / 12.f;
+        case 15: return log2f((float)v[13]) / 12.f;
         default: return (float)vk / fN;   // histogram, seeds, edges
     }
 }
@@ -74,7 +79,7 @@ __device__ __forceinline__ void feat_reduce(const FeatAcc &a, uint32_t (&v)[16],
     v[10] = __reduce_add_sync(0xffffffffu, a.sI);   // < 2^32: 4096 pixels x 65535
     v[11] = 0;
     v[12] = __reduce_add_sync(0xffffffffu, a.sJ);
-    v[13] = 0;
+    v[13] = __reduce_add_sync(0xffffffffu, a.npix);
     v[14] = __reduce_add_sync(0xffffffffu, a.sD);
     v[15] = __reduce_add_sync(0xffffffffu, a.n);
     sI2 = a.sI2;

@@ -102,7 +102,7 @@ __device__ __forceinline__ void scan_tile_stream(const ImageView &im, int y0, in
     for (int k = 0; k < D; k++)
         if (k < ns) stream_issue<WIDE, PAIR>(im, y0 - 1 + k, gx, hc, k >= 1 && k <= ny, lane, q[k]);
     uint32_t jPrev = 0, jCur = 0, iCur = 0, hPrev = 0, hCur = 0;
-    uint32_t h03 = 0, h47 = 0;   // FEATS: 8-bit histogram bins (at most 128 pixels per lane)
+    uint32_t h03 = 0, h47 = 0;   // FEATS: 8-bit histogram bins (at most 32 sampled pixels per lane)
     bool any = false, nok = false;
     for (int s0 = 0; s0 < ns; s0 += D) {
 #pragma unroll
@@ -118,7 +118,7 @@ __device__ __forceinline__ void scan_tile_stream(const ImageView &im, int y0, in
                     const uint32_t m = CONN == 8 ? max2(hPrev, max2(hCur, hN)) : max2(hCur, max2(jPrev, Jn));
                     any |= min2(iCur, m) != jCur;
                     nok |= max2(jCur, iCur) != iCur;
-                    if (FEATS) {
+                    if (FEATS && ((s - 2) % kFeatRowStep) == 0) {   // a sampled row (tile row s - 2)
                         const uint32_t iv = iCur, jv = jCur;
                         const uint32_t dv = max2(iv, jv) - jv;   // per half max(I - J, 0): no borrow
                         const uint32_t d8 = WIDE ? (dv >> 8) & 0x00FF00FFu : dv;
@@ -155,8 +155,10 @@ __device__ __forceinline__ void scan_tile_stream(const ImageView &im, int y0, in
     can = any;
     bad = nok;
     if (FEATS) {
-        fa.n = (uint32_t)ny * ((uint32_t)c0 + (uint32_t)c1);
-        fa.h03 = h03 - (2u * (uint32_t)ny - fa.n);   // pixels outside the image were counted in bin 0
+        const uint32_t nrs = (uint32_t)((ny + kFeatRowStep - 1) / kFeatRowStep);   // sampled rows
+        fa.n = nrs * ((uint32_t)c0 + (uint32_t)c1);
+        fa.npix = (uint32_t)ny * ((uint32_t)c0 + (uint32_t)c1);
+        fa.h03 = h03 - (2u * nrs - fa.n);   // columns outside the image were counted in bin 0
         fa.h47 = h47;
     }
 }

@@ -62,9 +62,9 @@ __device__ __forceinline__ int find_image(const SchedImage *tab, int n, uint32_t
 }
 
 // ---- features: one warp per block; lane c holds columns 2c and 2c + 1 of every row ------------
-// Exact integer sums per lane (8-bit packed histogram counters: at most 128 pixels per lane),
-// warp reductions, then lane 0 converts. Rows are read four at a time so that several loads
-// are in flight per warp; the edge test of a row needs the next row's mask, so it lags by one.
+// Exact integer sums per lane over the block's sampled rows (8-bit packed histogram counters:
+// at most 32 pixels per lane), warp reductions, then lane 0 converts. A sampled row is read
+// with the row below it, which the edge test needs.
 // Pixels (y, x) and (y, x + 1) of plane p (flipped), loaded with clamped addresses; the
 // caller masks the ones outside the block.
 __device__ __forceinline__ void feat_load(const SchedImage &im, const uint8_t *p, int y, int x, uint32_t &e,
@@ -128,8 +128,10 @@ __device__ __forceinline__ void feat_block_vec(const SchedImage &im, int y0, int
         }
         const bool has_down = !(g == RPG - 1 && k == NK - 1);
         const uint32_t right = __shfl_down_sync(0xffffffffu, iw[0], 1);   // next lane's first word
+        a.npix += PX;
+        const bool sampled = ((k * RPG + g) % kFeatRowStep) == 0;   // this lane's row of the block
 #pragma unroll
-        for (int w = 0; w < 4; w++) {
+        for (int w = 0; w < 4 && sampled; w++) {
 #pragma unroll
             for (int q = 0; q < PPW; q++) {
                 const uint32_t i = px_of<U16>(iw[w], q), j = px_of<U16>(jw[w], q);
@@ -171,7 +173,6 @@ __global__ void __launch_bounds__(256) features_kernel(const SchedImage *tab, in
         } else {
         const int c = x0 + 2 * lane;
         const bool ine = c < xe, ino = c + 1 < xe, inr = c + 2 < xe;   // this pair, and the next lane's
-        uint32_t pe = 0, po = 0;   // mask of the previous row (edges lag by one row)
         auto edges_of = [&](uint32_t ie, uint32_t io, uint32_t de, uint32_t dn, bool has_down) {
             // ie / io: a row's pair; de / dn: the pair below (ignored when !has_down)
             const uint32_t nxt = __shfl_down_sync(0xffffffffu, ie, 1);   // column 2c + 2
@@ -182,25 +183,18 @@ __global__ void __launch_bounds__(256) features_kernel(const SchedImage *tab, in
             if (ine) a.edges += (gxe + gye > thr);
             if (ino) a.edges += (gxo + gyo > thr);
         };
-        for (int y = y0; y < ye; y += 4) {
-            uint32_t Ie[4], Io[4], Je[4], Jo[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int yy = min(y + q, ye - 1);
-                feat_load(im, im.I, yy, c, Ie[q], Io[q]);
-                feat_load(im, im.J, yy, c, Je[q], Jo[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                if (y + q >= ye) break;   // warp-uniform
-                if (ine) feat_pixel(a, Ie[q], Je[q], u16);
-                if (ino) feat_pixel(a, Io[q], Jo[q], u16);
-                if (y + q > y0) edges_of(pe, po, Ie[q], Io[q], true);
-                pe = Ie[q];
-                po = Io[q];
-            }
+        // the sampled rows y0, y0 + kFeatRowStep, ... with the row below each (in the block)
+        for (int y = y0; y < ye; y += kFeatRowStep) {
+            uint32_t Ie, Io, Je, Jo, De, Do;
+            const bool down = y + 1 < ye;
+            feat_load(im, im.I, y, c, Ie, Io);
+            feat_load(im, im.J, y, c, Je, Jo);
+            feat_load(im, im.I, down ? y + 1 : y, c, De, Do);
+            if (ine) feat_pixel(a, Ie, Je, u16);
+            if (ino) feat_pixel(a, Io, Jo, u16);
+            edges_of(Ie, Io, De, Do, down);
         }
-        edges_of(pe, po, 0u, 0u, false);   // the block's last row has no row below
+        a.npix = (uint32_t)(ye - y0) * ((uint32_t)ine + (uint32_t)ino);
         }
 
         uint32_t v[16];

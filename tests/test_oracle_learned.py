@@ -11,16 +11,19 @@ from oracle import features, mlp
 from paper_1605_00930_gb300 import synth
 
 
-def _brute_block(marker, mask, op, by, bx, B=64):
+def _brute_block(marker, mask, op, by, bx, B=64, step=4):
+    """Features of one block, pixel by pixel: every `step`-th row of the block (rows 0, step,
+    ...) is summed; the edge test looks at the next row of the block, sampled or not; the
+    last feature counts every pixel of the block."""
     M = int(np.iinfo(mask.dtype).max)
     H, W = mask.shape
     ys = range(by * B, min(H, by * B + B))
     xs = range(bx * B, min(W, bx * B + B))
-    n = len(ys) * len(xs)
+    n = len(ys[::step]) * len(xs)
     hist = [0] * 8
     seeds = edges = 0
     sI = sI2 = sJ = sJ2 = sD = 0
-    for y in ys:
+    for y in ys[::step]:
         for x in xs:
             i, j = int(mask[y, x]), int(marker[y, x])
             if op == "erode":
@@ -39,7 +42,8 @@ def _brute_block(marker, mask, op, by, bx, B=64):
     mI, mJ = sI / n, sJ / n
     return np.array([h / n for h in hist] + [seeds / n, edges / n, mI / M,
                     math.sqrt(max(0.0, sI2 / n - mI * mI)) / M, mJ / M,
-                    math.sqrt(max(0.0, sJ2 / n - mJ * mJ)) / M, sD / n / M, math.log2(n) / 12])
+                    math.sqrt(max(0.0, sJ2 / n - mJ * mJ)) / M, sD / n / M,
+                    math.log2(len(ys) * len(xs)) / 12])
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
@@ -74,6 +78,13 @@ def test_features_hand_blocks():
     # a vertical step edge of height 20 > 16 between columns 0 and 1 of a 1 x 2 block
     f = features.block_features(np.zeros((1, 2), np.uint8), np.array([[0, 20]], np.uint8), "dilate", 0, 0)
     assert f[9] == 0.5
+    # rows 0 and 4 of a 5 x 2 block are sampled: mask rows 0, 200, 0, 0, 100 over marker 0 give
+    # d = 0 (bin 0) and 100 (bin 7, >= 64) on the sampled rows; row 0's pixels see the 200 below
+    # them (edges), row 4 has no row below in the block; the unsampled 200 adds nothing else
+    mask = np.array([[0, 0], [200, 200], [0, 0], [0, 0], [100, 100]], np.uint8)
+    f = features.block_features(np.zeros_like(mask), mask, "dilate", 0, 0)
+    assert f[0] == 0.5 and f[7] == 0.5 and f[1:7].sum() == 0
+    assert f[9] == 0.5 and f[10] == 50 / 255 and f[15] == math.log2(10) / 12
 
 
 def test_mlp_forward_hand_weights():

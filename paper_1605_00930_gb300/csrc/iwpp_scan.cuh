@@ -27,7 +27,7 @@ namespace iwpp {
 #define IWPP_STREAM_MINB 8    // CTAs (of 4 warps) per SM of the streaming scan
 #endif
 #ifndef IWPP_STREAM_FEATS_MINB
-#define IWPP_STREAM_FEATS_MINB 6   // the same with the feature sums
+#define IWPP_STREAM_FEATS_MINB 8   // the same with the feature sums (spills, but faster than 6 or 7: measured)
 #endif
 
 // One row of the stream as loaded; unpacked only when the row is used, so that the loads of

@@ -10,8 +10,9 @@
 // halo column pixel on their side. Loads run IWPP_STREAM_DEPTH rows ahead of the row
 // being tested, through a ring of registers, so every warp keeps that many rows in flight without
 // a break between tiles, and the image table is read once per tile. Rows are tested with a
-// sliding window of three rows; learned batches also add up the tile's feature sums
-// (iwpp_feat.cuh) and, as the warp owns the whole tile, write its 16 features directly.
+// sliding window of three rows; learned batches also add up the tile's feature sums over its
+// sampled rows (iwpp_feat.cuh) and, as the warp owns the whole tile, write its 16 features
+// directly.
 #pragma once
 #include <type_traits>
 

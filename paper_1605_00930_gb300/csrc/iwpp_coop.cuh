@@ -99,7 +99,7 @@ __device__ void visit_tile_coop(const EngineArgs &a, const ImageView &im, uint32
     constexpr int TH = kCoopStrip;
     using RT = RegTile<T, CONN, TH>;
     const typename RT::Smem s = RT::carve(wsmem);
-    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const uint32_t *hx = RT::halo_words(s, lane);
     const uint32_t lt = t - im.tile_base;
     const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
     const int y0 = ty * kCoopRows + TH * w, x0 = tx * RT::TW;
@@ -271,7 +271,7 @@ __device__ void scan_tile_coop(const EngineArgs &a, const ImageView &im, uint32_
     if (SWEEPS && a.sweep_only && sweeps == 0) return;   // the sweeps-only pass: nothing to do here
     const long long c0 = clock64();
     const typename RT::Smem s = RT::carve(wsmem);
-    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const uint32_t *hx = RT::halo_words(s, lane);
     const uint32_t lt = t - im.tile_base;
     const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
     const int y0 = ty * kCoopRows + TH * w, x0 = tx * RT::TW;
@@ -347,7 +347,7 @@ __device__ void scan_strip_coop(const EngineArgs &a, const ImageView &im, uint32
     if (y0 >= im.H) return;   // a strip below the image (warp-uniform): nothing in it can rise
     const long long c0 = clock64();
     const typename RT::Smem s = RT::carve(wsmem);
-    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const uint32_t *hx = RT::halo_words(s, lane);
     uint32_t J[TH], I[TH], jt, jb, it, ib;
     RT::load(im, s, y0, x0, J, I, jt, jb, it, ib, lane);
     bool bad = false;

@@ -53,12 +53,13 @@ struct RegTile {
         else return sizeof(T) == 2;
     }
     struct Smem {
-        uint32_t *hxJ;          // 2 x (TH + 2): [0..TH+1] left halo column << 16, [TH+2..] right halo column
+        uint32_t *hxJ;          // 2 x (TH + 2): [0..TH+1] left halo column, [TH+2..] right halo column << 16
+        uint32_t *hzero;        // TH + 2 zeros: the halo words of lanes 1..30
         uint32_t *hlI, *hrI;    // TH + 2: mask of the halo columns, index = row + 1
         uint32_t *col0, *col63; // TH: the tile's first and last column after a solve
         uint32_t *misc;         // 16: notification flags
     };
-    static constexpr size_t kWords = 4 * (TH + 2) + 2 * TH + 16;
+    static constexpr size_t kWords = 5 * (TH + 2) + 2 * TH + 16;
     static __host__ __device__ size_t smem_per_warp(uint32_t) { return (kWords * 4 + 15) & ~(size_t)15; }
     static size_t smem_bytes(uint32_t q) { return smem_per_warp(q) * kWarpsPerCta; }
 
@@ -66,6 +67,7 @@ struct RegTile {
         Smem s;
         uint32_t *w = reinterpret_cast<uint32_t *>(base);
         s.hxJ = w; w += 2 * (TH + 2);
+        s.hzero = w; w += TH + 2;
         s.hlI = w; w += TH + 2;
         s.hrI = w; w += TH + 2;
         s.col0 = w; w += TH;
@@ -132,8 +134,9 @@ struct RegTile {
                 li = ld1(im, im.I, el, false);
                 ri = ld1(im, im.I, er, false);
             }
-            s.hxJ[hr] = lin ? (lj ^ im.flip) << 16 : 0u;
-            s.hxJ[TH + 2 + hr] = rin ? rj ^ im.flip : 0u;
+            s.hxJ[hr] = lin ? lj ^ im.flip : 0u;
+            s.hxJ[TH + 2 + hr] = rin ? (rj ^ im.flip) << 16 : 0u;
+            s.hzero[hr] = 0u;
             if (withI) {
                 s.hlI[hr] = lin ? li ^ im.flip : 0u;
                 s.hrI[hr] = rin ? ri ^ im.flip : 0u;
@@ -232,8 +235,9 @@ struct RegTile {
         use(rjt, rit, y0 - 1, 0, y0 >= 1 && y0 - 1 < H, jt, it);
         use(rjb, rib, y0 + TH, TH + 1, y0 + TH < H, jb, ib);
         if (lane < TH + 2) {
-            s.hxJ[lane] = lin ? (lj ^ im.flip) << 16 : 0u;
-            s.hxJ[TH + 2 + lane] = rin ? rj ^ im.flip : 0u;
+            s.hxJ[lane] = lin ? lj ^ im.flip : 0u;
+            s.hxJ[TH + 2 + lane] = rin ? (rj ^ im.flip) << 16 : 0u;
+            s.hzero[lane] = 0u;
             s.hlI[lane] = lin ? li ^ im.flip : 0u;
             s.hrI[lane] = rin ? ri ^ im.flip : 0u;
         }
@@ -301,8 +305,9 @@ struct RegTile {
         jb = bin ? unpack_raw(im, rjb) ^ f2 : 0u;
         ib = bin ? unpack_raw(im, rib) ^ f2 : 0u;
         if (lane < TH + 2) {
-            s.hxJ[lane] = lin ? (lj ^ im.flip) << 16 : 0u;
-            s.hxJ[TH + 2 + lane] = rin ? rj ^ im.flip : 0u;
+            s.hxJ[lane] = lin ? lj ^ im.flip : 0u;
+            s.hxJ[TH + 2 + lane] = rin ? (rj ^ im.flip) << 16 : 0u;
+            s.hzero[lane] = 0u;
             s.hlI[lane] = lin ? li ^ im.flip : 0u;
             s.hrI[lane] = rin ? ri ^ im.flip : 0u;
         }
@@ -310,12 +315,19 @@ struct RegTile {
     }
 
     // Horizontal max of a packed row over (left, self, right); `h` is this lane's halo word
-    // (lane 0: left halo column << 16, lane 31: right halo column, others unused).
+    // (lane 0: the left halo pixel in the low half, lane 31: the right halo pixel in the high
+    // half, the other lanes 0). Lane 0's up shuffle and lane 31's down shuffle return their
+    // own pair, so their outside neighbour repeats a pixel of the pair that the max already
+    // holds, and h supplies the real one: one max instead of two lane selects.
     static __device__ __forceinline__ uint32_t hmax(uint32_t v, uint32_t h, int lane) {
-        uint32_t p = __shfl_up_sync(0xffffffffu, v, 1), n = __shfl_down_sync(0xffffffffu, v, 1);
-        if (lane == 0) p = h;
-        if (lane == 31) n = h;
-        return max2(v, max2(left_of(p, v), right_of(v, n)));
+        (void)lane;
+        const uint32_t p = __shfl_up_sync(0xffffffffu, v, 1), n = __shfl_down_sync(0xffffffffu, v, 1);
+        return max2(max2(v, h), max2(left_of(p, v), right_of(v, n)));
+    }
+
+    // This lane's halo words, index = row + 1 (lanes 1..30: zeros).
+    static __device__ __forceinline__ const uint32_t *halo_words(const Smem &s, int lane) {
+        return lane == 0 ? s.hxJ : (lane == 31 ? s.hxJ + TH + 2 : s.hzero);
     }
 
     // One down pass; returns this lane's mask of changed rows. For 8-connectivity the
@@ -379,7 +391,7 @@ struct RegTile {
         // this lane's pair as one clamp, even pixel first: (lo, hi)
         uint32_t G = min2(dup_hi(Ir), max2(dup_hi(A), __byte_perm(A, Ir, 0x5410)));
         if (lane == 0) {   // fold the west halo in: lane 0's map becomes a constant
-            const uint32_t c = min(G >> 16, max(G & 0xFFFFu, hxr >> 16));
+            const uint32_t c = min(G >> 16, max(G & 0xFFFFu, hxr & 0xFFFFu));
             G = c | (c << 16);
         }
 #pragma unroll
@@ -390,16 +402,16 @@ struct RegTile {
         }
         // every map is now a constant: the value leaving this lane's odd pixel
         const uint32_t E = __shfl_up_sync(0xffffffffu, G, 1);
-        const uint32_t u = lane == 0 ? hxr >> 16 : E & 0xFFFFu;
+        const uint32_t u = lane == 0 ? hxr & 0xFFFFu : E & 0xFFFFu;
         const uint32_t X = min2(Ir, max2(A, u));                      // even pixel (low half)
         return __byte_perm(X, G, 0x5410);
     }
 
-    // East-to-west pass over one packed row (lane 31: east halo pixel in the low half).
+    // East-to-west pass over one packed row (lane 31: east halo pixel in the high half).
     static __device__ __forceinline__ uint32_t row_ew(uint32_t A, uint32_t Ir, uint32_t hxr, int lane) {
         uint32_t G = min2(dup_lo(Ir), max2(dup_lo(A), __byte_perm(A, Ir, 0x7632)));   // odd pixel first
         if (lane == 31) {
-            const uint32_t c = min(G >> 16, max(G & 0xFFFFu, hxr & 0xFFFFu));
+            const uint32_t c = min(G >> 16, max(G & 0xFFFFu, hxr >> 16));
             G = c | (c << 16);
         }
 #pragma unroll
@@ -409,7 +421,7 @@ struct RegTile {
             if (lane + d < 32) G = C;
         }
         const uint32_t E = __shfl_down_sync(0xffffffffu, G, 1);
-        const uint32_t u = lane == 31 ? hxr & 0xFFFFu : E & 0xFFFFu;
+        const uint32_t u = lane == 31 ? hxr >> 16 : E & 0xFFFFu;
         const uint32_t Y = min2(Ir, max2(A, u << 16));                // odd pixel (high half)
         return __byte_perm(G, Y, 0x7610);
     }
@@ -503,8 +515,8 @@ struct RegTile {
                 if (r < TH - 1) { ml = max(ml, s.col0[r + 1]); mr = max(mr, s.col63[r + 1]); }
             }
             const uint32_t cl = min(s.hlI[r + 1], ml), cr = min(s.hrI[r + 1], mr);
-            if (cl > (s.hxJ[r + 1] >> 16)) vl = max(vl, cl);
-            if (cr > s.hxJ[TH + 2 + r + 1]) vr = max(vr, cr);
+            if (cl > s.hxJ[r + 1]) vl = max(vl, cl);
+            if (cr > (s.hxJ[TH + 2 + r + 1] >> 16)) vr = max(vr, cr);
         }
         vl = __reduce_max_sync(0xffffffffu, vl);
         vr = __reduce_max_sync(0xffffffffu, vr);
@@ -515,10 +527,10 @@ struct RegTile {
             if (CONN == 8) {   // corners
                 const uint32_t a0 = min(s.hlI[0], s.col0[0]), a6 = min(s.hlI[TH + 1], s.col0[TH - 1]);
                 const uint32_t a2 = min(s.hrI[0], s.col63[0]), a8 = min(s.hrI[TH + 1], s.col63[TH - 1]);
-                c0 = a0 > (s.hxJ[0] >> 16) ? a0 : 0u;
-                c6 = a6 > (s.hxJ[TH + 1] >> 16) ? a6 : 0u;
-                c2 = a2 > s.hxJ[TH + 2] ? a2 : 0u;
-                c8 = a8 > s.hxJ[2 * TH + 3] ? a8 : 0u;
+                c0 = a0 > s.hxJ[0] ? a0 : 0u;
+                c6 = a6 > s.hxJ[TH + 1] ? a6 : 0u;
+                c2 = a2 > (s.hxJ[TH + 2] >> 16) ? a2 : 0u;
+                c8 = a8 > (s.hxJ[2 * TH + 3] >> 16) ? a8 : 0u;
             }
             s.misc[0] = c0;
             s.misc[2] = c2;
@@ -610,7 +622,7 @@ template <typename T, int CONN, int TH>
 __device__ void scan_tile_reg(const EngineArgs &a, const ImageView &im, uint32_t t, uint8_t *wsmem, int lane) {
     using RT = RegTile<T, CONN, TH>;
     const typename RT::Smem s = RT::carve(wsmem);
-    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const uint32_t *hx = RT::halo_words(s, lane);
     const long long c0 = clock64();
     const uint32_t lt = t - im.tile_base;
     const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);
@@ -677,7 +689,7 @@ __device__ void visit_tile_reg(const EngineArgs &a, const ImageView &im, uint32_
 #endif
     using RT = RegTile<T, CONN, TH>;
     const typename RT::Smem s = RT::carve(wsmem);
-    const uint32_t *hx = s.hxJ + (lane == 31 ? TH + 2 : 0);
+    const uint32_t *hx = RT::halo_words(s, lane);
     const long long c0 = clock64();
     const uint32_t lt = t - im.tile_base;
     const int ty = (int)(lt / im.tiles_x), tx = (int)(lt % im.tiles_x);

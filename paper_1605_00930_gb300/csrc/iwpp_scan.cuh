@@ -64,7 +64,7 @@ __device__ __forceinline__ void stream_issue(const ImageView &im, int y, int gx,
 }
 
 // The row in the dilation domain: packed pair of J and I (0 outside the image) and this
-// lane's halo word (lane 0: left halo pixel << 16, lane 31: right halo pixel, as hmax wants).
+// lane's halo word (lane 0: left halo pixel, lane 31: right halo pixel << 16, as hmax wants).
 template <bool WIDE, bool PAIR>
 __device__ __forceinline__ void stream_unpack(const StreamRow &r, bool yin, uint32_t cm, uint32_t flip, bool hin,
                                               int lane, uint32_t &J, uint32_t &I, uint32_t &H) {
@@ -79,7 +79,7 @@ __device__ __forceinline__ void stream_unpack(const StreamRow &r, bool yin, uint
     const uint32_t f2 = flip | (flip << 16);
     J = yin ? (j ^ f2) & cm : 0u;
     I = yin ? (i ^ f2) & cm : 0u;
-    H = (yin && hin) ? (r.h ^ flip) << (lane == 0 ? 16 : 0) : 0u;
+    H = (yin && hin) ? (r.h ^ flip) << (lane == 31 ? 16 : 0) : 0u;
 }
 
 // One tile: rows y0 .. y0 + ny - 1 of the image (ny >= 1), streamed as rows y0 - 1 .. y0 + ny.

@@ -568,49 +568,59 @@ def run_ours(args, rank: int, world: int):
 
     # end to end through the C ABI from pinned host buffers, as a user streaming batches runs
     # it: per step the H2D copy of every marker and mask (the two arenas), the learned batch
-    # call and the D2H copy of every result. Two device buffer sets on two streams, so that one
-    # step's copies overlap the previous step's kernels (the kernels of consecutive steps still
-    # run one after the other: each step's call waits for the previous step's kernels).
+    # call and the D2H copy of every result. Three device buffer sets and three streams: input
+    # copies on one, the batch calls on another (consecutive steps' kernels run in order), the
+    # result copies on a third; a step's input copy waits only for the result copy out of the
+    # same buffer set three steps earlier, so the two copy directions and the kernels overlap.
     hm = torch.from_numpy(db.host_marker).pin_memory()
     hI = torch.from_numpy(db.host_mask).pin_memory()
-    db2 = DeviceBatch(head_cases, dev)
-    B2 = iwpp.Batch(db2.items, plan)
-    sets = [(db, F.Bl if sch is not None else F.Bs), (db2, B2)]
-    e2e_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    hos = [torch.empty_like(hm).pin_memory() for _ in range(2)]
+    dbs = [db] + [DeviceBatch(head_cases, dev) for _ in range(2)]
+    Bks = [F.Bl if sch is not None else F.Bs] + [iwpp.Batch(d.items, plan) for d in dbs[1:]]
+    K = len(dbs)
+    s_in, s_run, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    hos = [torch.empty_like(hm).pin_memory() for _ in range(K)]
 
     def e2e_run(nsteps):
-        prev = None
+        freed = [None] * K   # per buffer set: its last result copy has been read out
         for i in range(nsteps):
-            d, Bk = sets[i % 2]
-            s = e2e_streams[i % 2]
-            with torch.cuda.stream(s):
+            k = i % K
+            d, Bk = dbs[k], Bks[k]
+            with torch.cuda.stream(s_in):
+                if freed[k] is not None:
+                    s_in.wait_event(freed[k])
                 d.marker.copy_(hm, non_blocking=True)
                 d.mask.copy_(hI, non_blocking=True)
-                if prev is not None:
-                    s.wait_event(prev)
-                rc = sch.reconstruct(Bk, s) if sch is not None else Bk(stream=s)
-                if rc != 0:
-                    raise RuntimeError(f"batch call failed: {rc}")
-                prev = torch.cuda.Event()
-                prev.record(s)
-                hos[i % 2].copy_(d.marker, non_blocking=True)
+                loaded = torch.cuda.Event()
+                loaded.record(s_in)
+            s_run.wait_event(loaded)
+            rc = sch.reconstruct(Bk, s_run) if sch is not None else Bk(stream=s_run)
+            if rc != 0:
+                raise RuntimeError(f"batch call failed: {rc}")
+            done = torch.cuda.Event()
+            done.record(s_run)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(done)
+                hos[k].copy_(d.marker, non_blocking=True)
+                freed[k] = torch.cuda.Event()
+                freed[k].record(s_out)
 
-    e2e_run(2)
+    e2e_run(K)
     torch.cuda.synchronize()
-    n_e2e = max(4, min(args.steps, 10))
+    n_e2e = max(4, args.steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(e2e_streams[0])
-    e2e_streams[1].wait_event(e0)
+    e0.record(s_in)
+    s_run.wait_event(e0)
+    s_out.wait_event(e0)
     e2e_run(n_e2e)
-    e2e_streams[0].wait_stream(e2e_streams[1])
-    e1.record(e2e_streams[0])
+    s_in.wait_stream(s_run)
+    s_in.wait_stream(s_out)
+    e1.record(s_in)
     torch.cuda.synchronize()
     e2e_ts = [e0.elapsed_time(e1) / n_e2e]
-    ok = all(sets[k][1].status(e2e_streams[k]) == 0 for k in range(2))
+    ok = all(Bks[k].status(s_run) == 0 for k in range(K))
     if not ok or not all(np.array_equal(h.numpy(), head_arena) for h in hos):
         raise RuntimeError("end-to-end run failed or differs from the device-resident run")
-    del db2, B2, sets
+    del dbs, Bks
     e2e_ms = max_over_ranks(float(np.mean(e2e_ts)), world, dev)
     if rank != 0:
         return None
@@ -644,11 +654,14 @@ def run_ours(args, rank: int, world: int):
         "e2e": {"value": round(world * db.pixels / e2e_ms / 1e6, 3), "unit": UNIT,
                 "h2d_bytes_per_step": 2 * db.nbytes, "d2h_bytes_per_step": db.nbytes,
                 "ms_per_step": round(e2e_ms, 3),
+                "steps": n_e2e,
                 "form": ("per step: pinned H2D of every marker and mask (two arena copies), the learned "
                          "batch call through the C ABI (iwpp_reconstruct_batch_learned), D2H of every result; "
-                         "two device buffer sets on two streams: a step's copies overlap the previous step's "
-                         "kernels, the kernels of consecutive steps run in order; CUDA events around the "
-                         "steps, mean per step; inputs exceed L2 (no flush between steps)")},
+                         "three device buffer sets, input copies, batch calls and result copies on three "
+                         "streams: a step's input copy overlaps the previous step's kernels and the result "
+                         "copy before it, the kernels of consecutive steps run in order; CUDA events around "
+                         "all steps (pipeline fill and drain included), mean per step; inputs exceed L2 (no "
+                         "flush between steps)")},
         "gpu_launches": F.launches(form) * args.steps,
         "clocks": cs.summary(t0, t1),
         "estimator": estimator,

@@ -581,7 +581,8 @@ IWPP_API int iwpp_edt(const void *mask, uint32_t *site_out, uint32_t *dist2_out,
  * wave-queue entries processed (pops), entries created by the visits' initial
  * scans (seeds), wave steps run (row passes for the register solver, summed over
  * the strips for the cooperative one), and
- * the persistent workers' summed waiting time and processing time in ns.
+ * the persistent workers' summed waiting time and processing time in ns (cooperative
+ * solver: per CTA, its run time less its waiting time).
  * Host pointer out[6]. Synchronises `stream`. Returns IWPP_OK or IWPP_ERR_CUDA.
  */
 IWPP_API int iwpp_work_counters(const void *workspace, void *stream, uint64_t out[6]);

@@ -136,7 +136,9 @@ class ClockSampler:
 KERNEL_SOURCES = ["paper_1605_00930_gb300/csrc/iwpp_api.cu",
                   "paper_1605_00930_gb300/csrc/iwpp_engine.cuh", "paper_1605_00930_gb300/csrc/iwpp_host.h",
                   "paper_1605_00930_gb300/csrc/iwpp_kern_reg.cu", "paper_1605_00930_gb300/csrc/iwpp_regtile.cuh",
-                  "paper_1605_00930_gb300/csrc/iwpp_kern_coop.cu", "paper_1605_00930_gb300/csrc/iwpp_coop.cuh"]
+                  "paper_1605_00930_gb300/csrc/iwpp_kern_coop.cu", "paper_1605_00930_gb300/csrc/iwpp_coop.cuh",
+                  "paper_1605_00930_gb300/csrc/iwpp_scan.cuh", "paper_1605_00930_gb300/csrc/iwpp_feat.cuh",
+                  "paper_1605_00930_gb300/csrc/iwpp_spread.h", "paper_1605_00930_gb300/csrc/iwpp_sched.cu"]
 
 
 def kernel_digest() -> str:

@@ -221,3 +221,60 @@ def test_batch_tile_count_is_host_only(iwpp):
     assert iwpp.iwpp_batch_tile_count(imgs, p) == 1 + 2 * 2 + 4 * 1
     imgs[1].connectivity = 6
     assert iwpp.iwpp_batch_tile_count(imgs, p) == -1
+
+
+def _images(iwpp, shapes, conn=8):
+    P = iwpp.Image
+    imgs = (P * len(shapes))()
+    buf = (ctypes.c_uint8 * 64)()
+    a16 = (ctypes.addressof(buf) + 15) // 16 * 16
+    for i, (H, W) in enumerate(shapes):
+        imgs[i] = P(a16, a16, H, W, conn, 0, i % 2, 0)
+    return imgs, buf
+
+
+def test_batch_block_count_and_sched_layout_are_host_only(iwpp):
+    """Feature blocks are the 64 x 64 blocks of every image (partial blocks at the right and
+    bottom edges count); the scheduling workspace holds the features array at a 256-byte
+    aligned offset with room for every block's 16 floats."""
+    shapes = [(1, 1), (33, 64), (100, 31), (64, 65), (4096, 257), (129, 4097)]
+    imgs, buf = _images(iwpp, shapes)
+    nb = sum(((H + 63) // 64) * ((W + 63) // 64) for H, W in shapes)
+    assert iwpp.iwpp_batch_block_count(imgs) == nb
+    bp = iwpp.iwpp_default_batch_plan()
+    assert (bp.tile_h, bp.tile_w) == (iwpp.FEATURE_BLOCK, iwpp.FEATURE_BLOCK)
+    assert iwpp.iwpp_batch_tile_count(imgs, bp) == nb
+    total = iwpp.iwpp_sched_workspace_bytes(imgs, bp)
+    off = iwpp.iwpp_sched_features_offset(imgs, bp)
+    assert off >= 0 and off % 256 == 0
+    assert off + nb * iwpp.NFEAT * 4 <= total
+    # a plan whose tiles do not divide the feature block, an empty image and an empty batch
+    # are rejected
+    p = iwpp.iwpp_default_batch_plan()
+    p.tile_h, p.tile_w, p.local_solver = 48, 64, iwpp.IWPP_SOLVER_QUEUE
+    assert iwpp.iwpp_sched_workspace_bytes(imgs, p) == 0
+    assert iwpp.iwpp_sched_features_offset(imgs, p) == -1
+    imgs[2].W = 0
+    assert iwpp.iwpp_batch_block_count(imgs) == -1
+    assert iwpp.iwpp_sched_features_offset(imgs, bp) == -1
+    assert iwpp.iwpp_batch_block_count((iwpp.Image * 0)()) == -1
+
+
+def test_batch_launch_count(iwpp):
+    """Launch accounting of one batch call: per 32 image descriptors one table upload, then
+    the tile map, scan, compaction, queue finalisation (phases 1) and the drain (phases 2);
+    the learned call with features from the scan adds per 32 descriptors one schedule-table
+    upload, the MLP, the sort's keys, bucket scan and scatter, and the sweeps-only pass. For
+    512 images that is 21 and 42 launches, the counts the ncu launch list of the 512-image
+    batch shows per call."""
+    assert iwpp.iwpp_batch_launch_count(512, 3) == 21
+    assert iwpp.iwpp_batch_launch_count(512, 7) == 42
+    for n in (1, 31, 32, 33, 64, 65, 512, 513):
+        chunks = (n + 31) // 32
+        assert iwpp.iwpp_batch_launch_count(n, 1) == chunks + 4
+        assert iwpp.iwpp_batch_launch_count(n, 2) == 1
+        assert iwpp.iwpp_batch_launch_count(n, 3) == chunks + 5
+        assert iwpp.iwpp_batch_launch_count(n, 5) == 2 * chunks + 9
+        assert iwpp.iwpp_batch_launch_count(n, 7) == 2 * chunks + 10
+    for n, ph in [(0, 3), (-1, 3), (5, 0), (5, 4), (5, 8)]:
+        assert iwpp.iwpp_batch_launch_count(n, ph) == -1

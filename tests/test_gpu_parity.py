@@ -285,3 +285,17 @@ def test_work_counters(iw):
     _, R = gpu_run(iw, c.marker, c.mask, 8, "dilate")
     cnt = R.counters()
     assert cnt["visits"] >= 1 and cnt["pops"] >= cnt["seeds"] >= 0
+
+
+def test_coop_drain_counters(iw):
+    """The cooperative drain's counters (kept per CTA in shared memory, flushed at the end):
+    each counted visit starts with its four strips unsettled, and an unsettled strip runs a
+    down and an up pass, so the passes summed over the strips are at least 8 per visit; the
+    processing time is positive and the waiting time not negative."""
+    assert iw.iwpp_default_plan().local_solver == iw.IWPP_SOLVER_COOP
+    c = synth.tissue_case(512, 512, nblobs=20)
+    _, R = gpu_run(iw, c.marker, c.mask, 8, "dilate")
+    cnt = R.counters()
+    assert cnt["visits"] >= 1
+    assert cnt["waves"] >= 8 * cnt["visits"], cnt
+    assert cnt["busy_ns"] > 0 and cnt["idle_ns"] >= 0, cnt

@@ -66,3 +66,40 @@ def test_device_batch_arena_layout_on_cpu():
     db.restore()
     for o, c in zip(db.outputs(), cases):
         np.testing.assert_array_equal(o, c.marker)
+
+
+def test_reference_arm_prints_one_json_line(monkeypatch, capsys):
+    """`bench.py --impl reference` (the oracle arm, CPU only) on the 512^2 workload: one JSON
+    line with the contract's keys, the oracle as its CPU baseline and zero copy bytes."""
+    import json
+    import sys
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "noiseblur512",
+                                      "--steps", "2", "--warmup", "1"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    bench.main()
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 2
+    assert d["warmup"] == 3   # raised to the minimum of three
+    assert d["value"] > 0 and d["config"]["name"] == "noiseblur512" and d["config"]["pixels_per_step"] == 512 * 512
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == bench.host_cores()
+    assert "whole workload" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_samples_when_over_budget(monkeypatch):
+    """Over its time budget the reference arm times a bounded sample: for a single image the
+    first rows of it, stated in the line."""
+    import bench
+    monkeypatch.setattr(bench, "REFERENCE_BUDGET_S", 1e-4)
+
+    class A:
+        workload, steps, warmup = "noiseblur512", 2, 3
+    d = bench.run_reference(A, 0, 1)
+    assert d["config"]["pixels_per_step"] == 16 * 512   # at least 16 rows of the 512 x 512 image
+    assert "first 16 rows" in d["cpu_baseline"]["sample"]

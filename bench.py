@@ -499,11 +499,40 @@ def run_profile(args):
             "drain_kernel": drain_kernel_name(db, F.plan), "launches_per_step": F.launches(form)}
 
 
+def run_profile_ops():
+    """A lean run for profilers: one call each of the distance transform, the watershed and
+    SKIZ, in that order, on the 4096^2 inputs the full run times (run_edt's tissue mask above
+    60, run_watershed's inverted blob field with 2000 labelled markers, run_skiz's porous
+    domain with 2000 markers), so that an ncu selection of the three drains
+    (-k regex:"edt_drain|ws_drain|sk_drain" -c 3) takes one launch of each."""
+    import torch
+    from paper_1605_00930_gb300 import iwpp, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    f = synth.tissue_case().mask
+    H, W = f.shape
+    fg = torch.from_numpy((f > 60).astype(np.uint8)).to(dev)
+    site = torch.empty((H, W), dtype=torch.int32, device=dev)
+    T = iwpp.DistanceTransform(H, W, dev)
+    if T(fg, site, None, 8) != 0 or T.status() != 0:
+        raise RuntimeError("edt call failed")
+    rng = synth.rng_for(9)
+    markers = np.zeros((H, W), np.int32)
+    markers[rng.integers(0, H, 2000), rng.integers(0, W, 2000)] = np.arange(1, 2001)
+    iwpp.watershed(torch.from_numpy(markers).to(dev), torch.from_numpy((255 - f).astype(np.uint8)).to(dev), 8)
+    sk_markers, sk_mask = synth.porous_skiz_case()
+    iwpp.skiz(torch.from_numpy(sk_markers.astype(np.int32)).to(dev), torch.from_numpy(sk_mask).to(dev), 8)
+    torch.cuda.synchronize()
+    return {"profile_run": "operators", "calls": ["iwpp_edt", "iwpp_watershed", "iwpp_skiz"], "H": H, "W": W}
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_1605_00930_gb300 import build as B
     B.build()
     from paper_1605_00930_gb300 import iwpp
+    if args.profile_ops:
+        return run_profile_ops()
     if args.profile:
         return run_profile(args)
 
@@ -959,6 +988,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="profiler run: one batched form of the workload only (see run_profile)")
     ap.add_argument("--profile-form", default="batched_static", choices=["batched_static", "batched_learned", "plain"])
+    ap.add_argument("--profile-ops", action="store_true",
+                    help="profiler run: one call each of the distance transform, watershed and SKIZ (see run_profile_ops)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
